@@ -1,0 +1,454 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix:
+values printed in the paper's worked examples (Sec. 3), closed forms
+(Fresnel equations, critical angle, Brewster angle, exponential survival,
+escape from an absorbing sphere, geometric series of reflections), invariants
+(energy conservation R + T = 1, Stokes relations, transversality), textbook
+distributions (1 + cos^2 Rayleigh law, dipole sin^2 law, Lambert cosine law)
+and brute force (BVH == all-triangle argmin).  Each is chosen so that a
+plausible slip in the oracle (a dropped term, a wrong sign or index, a
+transposed operand) fails at least one of them."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle as O
+from paper_2203_14354_gb300 import geometry as g
+from tests.golden.load import paper_values
+
+PV = paper_values()
+N_LXE, N_GXE, N_Q = PV["n_lxe"], PV["n_gxe"], PV["n_quartz"]
+
+
+def binom_sigma(p, n):
+    return math.sqrt(max(p * (1 - p), 1e-12) / n)
+
+
+# ---------------------------------------------------------------- Philox ----
+def test_uniform_mapping_range():
+    assert O.uniform(0) == 2.0 ** -24
+    assert O.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    assert 0.0 < O.uniform(0x12345678) < 1.0
+
+
+def test_philox_counter_sensitivity_and_uniformity():
+    key = np.array([7, 11], np.uint32)
+    outs = np.array([O.philox([i, 0, 0, 0], key) for i in range(4096)], np.uint64)
+    # every counter word and key word changes the output
+    base = O.philox([1, 2, 3, 4], [5, 6])
+    for i in range(4):
+        c = [1, 2, 3, 4]
+        c[i] ^= 1
+        assert not np.array_equal(O.philox(c, [5, 6]), base)
+    assert not np.array_equal(O.philox([1, 2, 3, 4], [5, 7]), base)
+    # no repeats among 16k words; chi^2 of the top 6 bits is flat
+    flat = outs.ravel()
+    assert len(np.unique(flat)) == flat.size
+    hist = np.bincount((flat >> np.uint64(26)).astype(np.int64), minlength=64)
+    assert stats.chisquare(hist).pvalue > 1e-4
+    # bitwise balance: each of the 32 bits set about half of the time
+    bits = ((flat[:, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1)).mean(0)
+    assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / math.sqrt(flat.size))
+
+
+# --------------------------------------------------------------- Fresnel ----
+@pytest.mark.parametrize("n1,n2", [(N_LXE, N_GXE), (N_GXE, N_Q), (N_LXE, N_Q), (N_Q, N_LXE)])
+def test_fresnel_normal_incidence_closed_form(n1, n2):
+    f = O.fresnel(n1, n2, 1.0)
+    r0 = (n1 - n2) / (n1 + n2)
+    assert f["rs"] == pytest.approx(r0, abs=1e-15)
+    assert f["rp"] == pytest.approx(-r0, abs=1e-15)  # p basis = s x k flips at normal incidence
+    assert f["ts"] == pytest.approx(2 * n1 / (n1 + n2), abs=1e-15)
+
+
+def test_fresnel_paper_values_e1():
+    # Sec. 3: 6.5 % reflected at LXe/GXe, 4.6 % at GXe/quartz (normal incidence)
+    r1 = O.fresnel(N_LXE, N_GXE, 1.0)["rs"] ** 2
+    r2 = O.fresnel(N_GXE, N_Q, 1.0)["rs"] ** 2
+    # the paper prints these to 0.1 % (truncated): 6.58 % -> "6.5 %", 4.66 % -> "4.6 %"
+    assert 0.0 <= r1 - PV["e1_reflect_lxe_gxe"] < 0.001
+    assert 0.0 <= (1 - r1) ** 2 * r2 - PV["e1_reflect_gxe_quartz"] < 0.001
+    assert r1 == pytest.approx(0.065795, abs=1e-6)
+    assert r2 == pytest.approx(0.053254, abs=1e-6)
+
+
+@pytest.mark.parametrize("n1,n2", [(N_LXE, N_GXE), (N_GXE, N_Q), (N_LXE, N_Q), (N_Q, N_GXE)])
+def test_fresnel_energy_conservation_and_stokes(n1, n2):
+    for th in np.linspace(0.0, 89.0, 90):
+        ci = math.cos(math.radians(th))
+        f = O.fresnel(n1, n2, ci)
+        if f["tir"]:
+            continue
+        ct = f["cos_t"]
+        # Snell
+        assert n1 * math.sqrt(1 - ci * ci) == pytest.approx(n2 * math.sqrt(1 - ct * ct), abs=1e-12)
+        flux = n2 * ct / (n1 * ci)
+        assert f["rs"] ** 2 + flux * f["ts"] ** 2 == pytest.approx(1.0, abs=1e-12)
+        assert f["rp"] ** 2 + flux * f["tp"] ** 2 == pytest.approx(1.0, abs=1e-12)
+        # Stokes relations: r' = -r, t t' = 1 - r^2 (reverse path n2 -> n1 at the refraction angle)
+        b = O.fresnel(n2, n1, ct)
+        assert b["rs"] == pytest.approx(-f["rs"], abs=1e-12)
+        assert b["rp"] == pytest.approx(-f["rp"], abs=1e-12)
+        assert f["ts"] * b["ts"] == pytest.approx(1 - f["rs"] ** 2, abs=1e-12)
+        assert f["tp"] * b["tp"] == pytest.approx(1 - f["rp"] ** 2, abs=1e-12)
+
+
+def test_brewster_and_critical_angles():
+    # Brewster: tan(theta_B) = n2/n1 -> r_p = 0
+    tb = math.atan(N_GXE / N_LXE)
+    assert abs(O.fresnel(N_LXE, N_GXE, math.cos(tb))["rp"]) < 1e-12
+    assert math.degrees(tb) == pytest.approx(30.61, abs=0.01)
+    # critical angles: Sec. 3 (TIR at LXe/GXe at the expected angle; 75 deg on LXe/quartz reflects fully)
+    for n1, n2, deg in [(N_LXE, N_GXE, 36.279), (N_LXE, N_Q, 71.217)]:
+        tc = math.asin(n2 / n1)
+        assert math.degrees(tc) == pytest.approx(deg, abs=1e-3)
+        assert not O.fresnel(n1, n2, math.cos(tc - 1e-6))["tir"]
+        assert O.fresnel(n1, n2, math.cos(tc + 1e-6))["tir"]
+    assert O.fresnel(N_LXE, N_Q, math.cos(math.radians(75.0)))["tir"]
+
+
+def _basis_case(theta_deg, pol_angle):
+    th = math.radians(theta_deg)
+    k = np.array([math.sin(th), 0.0, -math.cos(th)])
+    N = np.array([0.0, 0.0, 1.0])
+    s = np.cross(k, N)
+    s /= np.linalg.norm(s)
+    p = np.cross(s, k)
+    eps = math.cos(pol_angle) * s + math.sin(pol_angle) * p
+    return k, N, s, eps
+
+
+def test_dielectric_geometry_and_polarisation():
+    for th in (10.0, 25.0, 35.0, 50.0, 80.0):
+        for pa in (0.0, 0.7, 1.5707963):
+            k, N, s, eps = _basis_case(th, pa)
+            for n1, n2 in [(N_LXE, N_GXE), (N_GXE, N_Q)]:
+                for u in (1e-9, 1 - 1e-9):
+                    refl, ko, eo, pr = O.dielectric(k, eps, N, n1, n2, u)
+                    assert abs(np.linalg.norm(ko) - 1) < 1e-12 and abs(np.linalg.norm(eo) - 1) < 1e-12
+                    assert abs(ko @ eo) < 1e-12
+                    ci = -k @ N
+                    if refl:
+                        assert ko @ N == pytest.approx(ci, abs=1e-12)          # law of reflection
+                        assert ko[0] == pytest.approx(k[0], abs=1e-12)
+                    else:
+                        st = n1 / n2 * math.sqrt(1 - ci * ci)
+                        assert ko[0] == pytest.approx(st, abs=1e-12)            # Snell, in the plane
+                        assert ko @ N < 0
+                    # P(reflect) = cs^2 Rs + cp^2 Rp
+                    f = O.fresnel(n1, n2, ci)
+                    cs = eps @ s
+                    want = 1.0 if f["tir"] else cs * cs * f["rs"] ** 2 + (1 - cs * cs) * f["rp"] ** 2
+                    assert pr == pytest.approx(want, abs=1e-12)
+                    assert refl == (u < want)
+
+
+def test_brewster_reflection_is_s_polarised():
+    tb = math.degrees(math.atan(N_GXE / N_LXE))
+    k, N, s, eps = _basis_case(tb, 0.6)
+    refl, ko, eo, pr = O.dielectric(k, eps, N, N_LXE, N_GXE, 1e-12)
+    assert refl
+    assert abs(abs(eo @ s) - 1.0) < 1e-9
+
+
+def test_normal_incidence_keeps_photon():
+    # Appendix item 1: plane of incidence undefined at normal incidence
+    k = np.array([0.0, 0.0, -1.0])
+    N = np.array([0.0, 0.0, 1.0])
+    eps = np.array([1.0, 0.0, 0.0])
+    refl, ko, eo, pr = O.dielectric(k, eps, N, N_LXE, N_GXE, 1e-9)
+    assert refl and np.allclose(ko, [0, 0, 1]) and abs(abs(eo[0]) - 1) < 1e-12
+    assert pr == pytest.approx(((N_LXE - N_GXE) / (N_LXE + N_GXE)) ** 2, abs=1e-12)
+    refl, ko, eo, pr = O.dielectric(k, eps, N, N_LXE, N_GXE, 1 - 1e-9)
+    assert not refl and np.allclose(ko, k) and abs(abs(eo[0]) - 1) < 1e-12
+
+
+# ------------------------------------------------------------- Rayleigh -----
+def test_rayleigh_dipole_laws():
+    rng = np.random.default_rng(5)
+    n = 40000
+    cos_th, cos_psi = np.empty(n), np.empty(n)
+    for i in range(n):
+        k = rng.normal(size=3)
+        k /= np.linalg.norm(k)
+        e = rng.normal(size=3)
+        e -= (e @ k) * k
+        e /= np.linalg.norm(e)
+        ko, eo = O.rayleigh(k, e, pid=i, step=3, seed=9)
+        assert abs(ko @ eo) < 1e-9 and abs(np.linalg.norm(eo) - 1) < 1e-9
+        cos_th[i] = k @ ko
+        cos_psi[i] = e @ ko
+    # unpolarised marginal: density (3/8)(1 + c^2) on [-1, 1]; <c^2> = 2/5
+    cdf_th = lambda c: (3 * (c + 1) + (c ** 3 + 1)) / 8
+    assert stats.kstest(cos_th, cdf_th).pvalue > 1e-4
+    assert np.mean(cos_th ** 2) == pytest.approx(0.4, abs=5 * 0.3 / math.sqrt(n))
+    # relative to the polarisation: density (3/4)(1 - c^2) (dipole sin^2 law)
+    cdf_psi = lambda c: (3 * (c + 1) - (c ** 3 + 1)) / 4
+    assert stats.kstest(cos_psi, cdf_psi).pvalue > 1e-4
+    assert np.mean(cos_psi ** 2) == pytest.approx(0.2, abs=5 * 0.25 / math.sqrt(n))
+
+
+def test_lambert_cosine_law():
+    N = np.array([0.3, -0.4, math.sqrt(1 - 0.25)])
+    n = 30000
+    c = np.empty(n)
+    for i in range(n):
+        ko, eo = O.lambert(N, pid=i, step=1, seed=4)
+        c[i] = ko @ N
+        assert abs(ko @ eo) < 1e-9
+    assert c.min() > 0
+    assert stats.kstest(c, lambda x: np.clip(x, 0, 1) ** 2).pvalue > 1e-4
+
+
+# ------------------------------------------------------------ intersection --
+def test_intersection_axis_aligned_square_closed_form():
+    # the square z = 10, |x|,|y| <= 5 as two triangles
+    verts = np.array([[-5, -5, 10], [5, -5, 10], [5, 5, 10], [-5, 5, 10]], np.float32)
+    tris = np.array([[0, 1, 2], [0, 2, 3]], np.uint32)
+    z8 = np.zeros(2, np.uint8)
+    det = g.Detector("sq", verts, tris, z8, z8.copy(), np.full(2, g.SURF_NONE, np.uint16), np.full(2, -1, np.int32),
+                     [g.Material("m", 1.0)], [], np.zeros(0, np.int32), np.zeros((0, 3), np.float32),
+                     g.Source(g.SRC_POINT))
+    o = O.Oracle(det)
+    rng = np.random.default_rng(0)
+    n = 2000
+    org = np.zeros((n, 3), np.float32)
+    org[:, :2] = rng.uniform(-4, 4, (n, 2))
+    dz = np.ones(n, np.float32)
+    dirs = np.stack([rng.uniform(-0.1, 0.1, n), rng.uniform(-0.1, 0.1, n), dz], 1).astype(np.float32)
+    hit, t = o.trace(org, dirs)
+    land = org[:, :2] + 10 * dirs[:, :2]
+    inside = np.all(np.abs(land) < 4.999, 1)
+    assert np.all(hit[inside] != 0xFFFFFFFF)
+    np.testing.assert_allclose(t[inside], 10.0, rtol=2e-7)
+    # triangle choice matches which side of the diagonal y = x the ray lands on
+    side = land[inside, 1] < land[inside, 0]
+    assert np.array_equal(hit[inside] == 0, side)
+    # rays pointing away miss; tmax clips; skip excludes
+    hit2, _ = o.trace(org, -dirs)
+    assert np.all(hit2 == 0xFFFFFFFF)
+    hit3, _ = o.trace(org, dirs, tmax=np.full(n, 9.9, np.float32))
+    assert np.all(hit3 == 0xFFFFFFFF)
+    hit4, _ = o.trace(org[inside], dirs[inside], skip=hit[inside])
+    assert np.all(hit4 == 0xFFFFFFFF)
+
+
+def test_bvh_equals_brute_force_on_soup():
+    det = g.random_soup(3000, seed=3)
+    o = O.Oracle(det)
+    rng = np.random.default_rng(1)
+    n = 3000
+    org = rng.uniform(-120, 120, (n, 3)).astype(np.float32)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d.astype(np.float32)
+    # aim a third of the rays exactly at vertices and edge midpoints (ties, shared edges)
+    tv = det.verts[det.tris]
+    m = n // 3
+    tgt = np.concatenate([tv[:m // 2, 0], (0.5 * (tv[m // 2:m, 0] + tv[m // 2:m, 1]))])
+    dd = tgt - org[:m]
+    d[:m] = (dd / np.linalg.norm(dd, axis=1, keepdims=True)).astype(np.float32)
+    skip = rng.integers(0, det.n_tris, n).astype(np.uint32)
+    skip[::2] = 0xFFFFFFFF
+    tmax = np.where(rng.uniform(size=n) < 0.3, rng.uniform(1, 200, n), np.inf).astype(np.float32)
+    hb, tb = o.trace(org, d, skip, tmax, brute=True)
+    hv, tv2 = o.trace(org, d, skip, tmax, brute=False)
+    assert np.array_equal(hb, hv)
+    assert np.array_equal(tb, tv2)
+    assert (hb != 0xFFFFFFFF).sum() > n // 4
+
+
+def test_watertight_closed_sphere():
+    det = g.icosphere(50.0, subdiv=3)
+    o = O.Oracle(det)
+    tv = det.verts[det.tris].astype(np.float64)
+    rng = np.random.default_rng(2)
+    # from interior points, aim exactly at every vertex and at edge midpoints
+    targets = np.concatenate([det.verts.astype(np.float64), 0.5 * (tv[:, 0] + tv[:, 1])])
+    org = rng.uniform(-10, 10, (targets.shape[0], 3))
+    d = targets - org
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    hit, t = o.trace(org.astype(np.float32), d.astype(np.float32))
+    assert np.all(hit != 0xFFFFFFFF)
+
+
+# ------------------------------------------------ full tracker: worked examples
+def _beam(n, pos, theta_deg, seed=1, spread=10.0):
+    rng = np.random.default_rng(seed)
+    p = np.tile(np.asarray(pos, np.float32), (n, 1))
+    p[:, 0] += rng.uniform(-spread, spread, n)
+    p[:, 1] += rng.uniform(-spread, spread, n)
+    th = math.radians(theta_deg)
+    d = np.tile(np.array([math.sin(th), 0, math.cos(th)], np.float32), (n, 1))
+    a = rng.uniform(0, 2 * np.pi, n)
+    s = np.array([0, 1, 0], np.float32)
+    pp = np.array([math.cos(th), 0, -math.sin(th)], np.float32)
+    pol = (np.cos(a)[:, None] * s + np.sin(a)[:, None] * pp).astype(np.float32)
+    return p, d, pol
+
+
+def test_worked_example_e1_reflection_series():
+    """Sec. 3 first check: 11.2 % bottom / 88.8 % top for photons sent straight up."""
+    det = g.layered_box()
+    o = O.Oracle(det)
+    n = 200_000
+    res = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=_beam(n, (0, 0, -50), 0.0))
+    r1 = ((N_LXE - N_GXE) / (N_LXE + N_GXE)) ** 2
+    r2 = ((N_GXE - N_Q) / (N_GXE + N_Q)) ** 2
+    bottom = r1 + (1 - r1) ** 2 * r2 / (1 - r1 * r2)
+    frac = res["lce"] / n
+    assert abs(frac[0] - bottom) < 4 * binom_sigma(bottom, n)
+    assert abs(frac[1] - (1 - bottom)) < 4 * binom_sigma(bottom, n)
+    assert round(frac[0], 3) == pytest.approx(PV["e1_bottom"], abs=0.0015)
+    assert round(frac[1], 3) == pytest.approx(PV["e1_top"], abs=0.0015)
+    assert res["fates"][O.ESCAPED] == 0 and res["fates"][O.GEOM_ERR] == 0
+
+
+def test_worked_example_e2_total_internal_reflection():
+    """Sec. 3 second check: 75 deg on the LXe/quartz window reflects 100 %."""
+    det = g.layered_box(with_gas=False)
+    o = O.Oracle(det)
+    n = 50_000
+    res = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=_beam(n, (0, 0, -20), 75.0, spread=5))
+    assert res["lce"][1] == 0
+    assert PV["e2_tir_fraction_75deg"] == 1.0
+    # just below the critical angle (71.2 deg) some photons enter the window
+    res2 = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=_beam(n, (0, 0, -20), 70.0, spread=5))
+    assert res2["lce"][1] > 0
+
+
+def test_critical_angle_lxe_gxe_e3():
+    det = g.layered_box()
+    o = O.Oracle(det)
+    n = 50_000
+    for th, want_top in ((36.5, False), (36.0, True)):
+        res = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=_beam(n, (0, 0, -50), th, spread=5))
+        assert (res["lce"][1] > 0) == want_top
+
+
+# --------------------------------------------- full tracker: closed forms ----
+def test_bulk_absorption_survival_exp():
+    lam = 100.0
+    det = g.icosphere(100.0, subdiv=5, abs_len_mm=lam)
+    o = O.Oracle(det)
+    n = 100_000
+    res = o.propagate(n)
+    p = math.exp(-100.0 / lam)
+    assert abs(res["lce"][0] / n - p) < 4 * binom_sigma(p, n) + 2e-4
+    assert res["fates"][O.BULK_ABS] + res["lce"].sum() == n
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.1])
+def test_escape_from_absorbing_sphere(tau):
+    R = 100.0
+    det = g.icosphere(R, subdiv=5, abs_len_mm=R / tau)
+    det.source = g.Source(g.SRC_BALL, 0, radius=R * 0.999)
+    o = O.Oracle(det)
+    n = 100_000
+    res = o.propagate(n, seed=3)
+    P = 3.0 / (8 * tau ** 3) * (2 * tau ** 2 - 1 + (1 + 2 * tau) * math.exp(-2 * tau))
+    assert abs(res["lce"][0] / n - P) < 4 * binom_sigma(P, n) + 2e-3
+
+
+def test_rayleigh_mean_free_path_and_time():
+    lam, R = 80.0, 100.0
+    det = g.icosphere(R, subdiv=5, ray_len_mm=lam, n_medium=N_LXE)
+    o = O.Oracle(det)
+    n = 100_000
+    res = o.propagate(n, per_photon=True, seed=5)
+    direct = res["steps"] == 1
+    p = math.exp(-R / lam)
+    assert abs(direct.mean() - p) < 4 * binom_sigma(p, n) + 2e-4
+    # unscattered photons arrive after R * n / c (within the tessellation depth)
+    t_exp = R * N_LXE / 299.792458
+    assert np.all(np.abs(res["time"][direct] - t_exp) < 1e-3 * t_exp)
+    # without absorption every photon is eventually detected
+    assert res["lce"][0] == n
+
+
+def test_mirror_sphere_normal_incidence_series():
+    """Radial photons hit a mirror sphere at normal incidence every 2R of
+    path (Appendix item 1: such photons must be reflected, not dropped)."""
+    lam, R = 300.0, 100.0
+    det = g.icosphere(R, subdiv=6, surface_type=g.REFLECTOR, abs_len_mm=lam)
+    det.surfaces[0] = g.Surface("mirror", g.REFLECTOR, reflectivity=1.0, spec_frac=1.0)
+    o = O.Oracle(det)
+    n = 50_000
+    res = o.propagate(n, per_photon=True, seed=2)
+    assert np.all(res["fate"] == O.BULK_ABS)
+    q = math.exp(-R / lam)
+    mean_steps = 1 + q / (1 - q * q)
+    sd = np.std(res["steps"])
+    assert abs(res["steps"].mean() - mean_steps) < 5 * sd / math.sqrt(n)
+
+
+def test_reflector_absorption_geometric():
+    R_ptfe = 0.8
+    det = g.icosphere(100.0, subdiv=4, surface_type=g.REFLECTOR)
+    det.surfaces[0] = g.Surface("ptfe", g.REFLECTOR, reflectivity=R_ptfe, spec_frac=0.0)
+    o = O.Oracle(det)
+    n = 50_000
+    res = o.propagate(n, per_photon=True, seed=8)
+    assert np.all(res["fate"] == O.SURF_ABS)
+    mean = 1 / (1 - R_ptfe)
+    sd = math.sqrt(R_ptfe) / (1 - R_ptfe)
+    assert abs(res["steps"].mean() - mean) < 5 * sd / math.sqrt(n)
+
+
+def test_electrode_transparency():
+    T, Rw = 0.9, 0.3
+    det = g.electrode_box(T, Rw)
+    o = O.Oracle(det)
+    n = 100_000
+    res = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, 0), explicit=_beam(n, (0, 0, -50), 0.0))
+    assert abs(res["lce"][1] / n - T) < 4 * binom_sigma(T, n)
+    absorbed = res["fates"][O.N_FIXED + 2 + 2]  # surface id 2 (electrode) after 2 materials
+    pa = (1 - T) * (1 - Rw)
+    assert abs(absorbed / n - pa) < 4 * binom_sigma(pa, n)
+
+
+def test_quantum_efficiency_and_tallies_consistent():
+    det = g.small_tpc()
+    o = O.Oracle(det)
+    n = 60_000
+    res = o.propagate(n, per_photon=True, seed=11)
+    f = res["fates"]
+    assert f[:7].sum() == n
+    assert f[7] == res["steps"].sum()
+    assert res["lce"].sum() == f[O.DETECTED] + f[O.QE_FAIL]
+    assert res["det"].sum() == f[O.DETECTED] == res["hist"].sum()
+    qe = f[O.DETECTED] / res["lce"].sum()
+    assert abs(qe - 0.3) < 4 * binom_sigma(0.3, res["lce"].sum())
+    assert f[O.ESCAPED] == 0 and f[O.GEOM_ERR] == 0 and f[O.TRUNCATED] == 0
+    # per-photon and aggregate agree
+    det_ph = res["fate"] == O.DETECTED
+    assert np.array_equal(np.bincount(res["detail"][det_ph], minlength=det.n_pmts), res["det"])
+
+
+# ------------------------------------------------------------------ source --
+def test_volume_source_uniform_isotropic():
+    det = g.small_tpc()
+    o = O.Oracle(det)
+    n = 100_000
+    pos, dirs, pol, med = o.sample_source(n, seed=1)
+    r = np.hypot(pos[:, 0], pos[:, 1])
+    assert r.max() <= 100.0 and pos[:, 2].min() >= -100 and pos[:, 2].max() <= 0
+    # area fraction inside r < 50 of the 64-gon
+    area64 = 0.5 * 64 * 100.0 ** 2 * math.sin(2 * math.pi / 64)
+    p = math.pi * 50 ** 2 / area64
+    assert abs((r < 50).mean() - p) < 4 * binom_sigma(p, n)
+    assert stats.kstest((pos[:, 2] + 100) / 100, "uniform").pvalue > 1e-4
+    assert stats.kstest((dirs[:, 2] + 1) / 2, "uniform").pvalue > 1e-4
+    phi = np.arctan2(dirs[:, 1], dirs[:, 0])
+    assert stats.kstest((phi + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-4
+    assert np.max(np.abs((pol * dirs).sum(1))) < 1e-12
+    assert np.all(med == g.LXE)
+
+
+def test_generated_meshes_are_closed():
+    for det in (g.small_tpc(), g.scaled_tpc(), g.layered_box(), g.icosphere(10, 2), g.electrode_box()):
+        t = det.tris.astype(np.int64)
+        e = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]]), 1)
+        _, cnt = np.unique(e, axis=0, return_counts=True)
+        assert np.all(cnt >= 2), det.name
