@@ -1,0 +1,290 @@
+"""Benchmark: photons propagated to fate per second on the DARWIN-scale mesh.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one lxo_propagate of a batch of photons (default 1e8) uniform in
+the active LXe volume of the DARWIN-scale detector (24-sided PTFE wall inscribed
+in r = 1300 mm, 889 + 889 3-inch PMTs, gate / anode / cathode as hexagonal
+216 um wire meshes at 5 mm pitch: 1.78e7 triangles), all interactions on,
+through the whole path (source sampling, BVH traversal, bulk sampling,
+Fresnel / TIR, reflectors, wire meshes, photocathodes, tallies).  The BVH
+(1.3 GB) is larger than L2, so no flush is needed between steps.
+
+Under torchrun each rank takes its own photon-id range (weak scaling; no
+collective on the data path); the timing is the max over ranks.
+
+--impl reference times the CPU oracle (the plain scalar C tracker) on the host
+cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "photons/sec to fate, DARWIN mesh, 1 GB300"
+UNIT = "photons/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--photons", type=float, default=1e8, help="photons per rank per step")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(n, world):
+    return {"workload": "DARWIN-scale dual-phase TPC forward: 24-gon PTFE wall r=1300 mm, 889+889 3-inch PMTs, "
+                        "gate/anode/cathode hex wire meshes 216 um @ 5 mm, 1.78e7 triangles; photons uniform in the "
+                        "active LXe, isotropic, random linear polarisation, t=0, 175 nm",
+            "photons_per_step": int(n) * world, "photons_per_rank": int(n), "triangles": 17813848,
+            "lxe_abs_m": 50, "lxe_rayleigh_cm": 40, "ptfe_R": [0.95, 0.70], "qe": 0.3,
+            "time_bins_ns": "1000 x 1 ns + overflow", "l2": "inputs larger than L2 (BVH 1.3 GB), no flush",
+            "parallelism": f"photon-id ranges per rank x{world}" if world > 1 else "single GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline(det, target_s):
+    """The oracle as it stands, on all host cores, on a bounded sample."""
+    import oracle
+    orc = oracle.Oracle(det)
+    cores = os.cpu_count() or 1
+    n0 = 20000
+    t0 = time.perf_counter()
+    orc.propagate(n0, base=0, seed=12345, threads=cores)
+    dt0 = time.perf_counter() - t0
+    n = int(min(5e7, max(n0, n0 * target_s / max(dt0, 1e-3))))
+    t0 = time.perf_counter()
+    res = orc.propagate(n, base=n0, seed=12345, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+            "sample": f"{n} photons of the same workload (seed 12345), {dt:.1f} s wall on {res['threads']} threads; "
+                      f"scene build excluded"}, res, n
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2203_14354_gb300 import geometry
+    det = geometry.darwin()
+    import oracle
+    orc = oracle.Oracle(det)
+    cores = os.cpu_count() or 1
+    per_step = max(20000, int(args.cpu_seconds * 90000 * cores / 8 / max(args.steps, 1)))
+    per_step = min(per_step, 2_000_000)
+    for w in range(args.warmup):
+        orc.propagate(min(per_step, 20000), base=w * per_step, seed=999, threads=cores)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        orc.propagate(per_step, base=(args.warmup + s) * per_step, seed=999, threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 physics / f32 intersection", "data": "synthetic",
+            "impl": "reference",
+            "config": dict(workload_config(per_step, 1), sample=f"{per_step} photons per step on the CPU"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} photons per step x {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2203_14354_gb300 import geometry, Tracker
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n = int(args.photons)
+    det = geometry.darwin()
+    t0 = time.perf_counter()
+    trk = Tracker(det, device=local)
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    base0 = rank * n * (args.warmup + args.steps + 4)
+    out = trk.alloc_results(1000)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(k):
+        for v in out.values():
+            v.zero_()
+        trk.propagate(n, base=base0 + k * n, seed=1, out=out, sync=False)
+
+    for w in range(args.warmup):
+        step(w)
+    trk.sync()
+    # per-step timing of the propagation kernel alone (events on the launching stream)
+    k_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for k in range(args.steps):
+            for v in out.values():
+                v.zero_()
+            k_start[k].record(stream)
+            trk.propagate(n, base=base0 + (args.warmup + k) * n, seed=1, out=out, sync=False)
+            k_end[k].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    trk.sync()
+    barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in zip(k_start, k_end)]
+    fates = out["fates"].cpu().numpy()
+    lce = out["lce"].cpu().numpy()
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * n * args.steps / (elapsed_ms / 1e3)
+
+    # traversal work of the same batch (separate, untimed launch of the counting build)
+    st_out = trk.alloc_results(1000)
+    trk.propagate(n, base=base0 + args.warmup * n, seed=1, out=st_out, stats=True)
+    stats = st_out["stats"].cpu().numpy().astype(np.float64)
+    steps_total, nodes, leaves, tris = stats
+    bytes_per_step = (nodes * 64 + tris * 48) / steps_total
+    kern_s = statistics.mean(kern_ms) / 1e3
+    achieved = steps_total * bytes_per_step / kern_s / 1e9
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    # end to end through the C ABI with host result buffers (copies in the timed region)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    host = None
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        host = trk.propagate_host(n, base=base0 + (args.warmup + args.steps + k) * n, seed=2)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    P = trk.n_channels
+    d2h = 4 * (2 * P + P * 1001) + 8 * trk.n_fates
+    import ctypes
+    from paper_2203_14354_gb300 import _capi
+    h2d = ctypes.sizeof(_capi.lxo_source) + ctypes.sizeof(_capi.lxo_run_params)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = cpu_baseline(det, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(n, world),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "peak_source": peak_kind,
+                         "algorithmic_bytes": "per photon step: BVH nodes visited x 64 B + triangles tested x 48 B",
+                         "per_step": {"nodes": nodes / steps_total, "leaves": leaves / steps_total,
+                                      "triangles": tris / steps_total, "bytes": bytes_per_step},
+                         "steps_per_photon": steps_total / n, "kernel_ms": statistics.mean(kern_ms)},
+            "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * 1,
+            "clocks": clk.summary(),
+            "physics": {"lce": float(lce.sum()) / n, "steps_per_photon": float(fates[7]) / n,
+                        "escaped": int(fates[4]), "geom_err": int(fates[6]), "truncated": int(fates[5])},
+            "setup_s": setup_s, "bvh": {k: v for k, v in trk.bvh_info.items()},
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * lxo.h -- C ABI of the GB300 optical-photon tracker for liquid-xenon TPCs.
+ *
+ * The library propagates 175 nm scintillation photons, one photon per GPU
+ * lane, through a triangle-mesh detector to their fate, PMT channel and
+ * arrival time: exponential bulk absorption and Rayleigh scattering, polarised
+ * Fresnel reflection / refraction with total internal reflection at
+ * dielectric boundaries, reflectivity-parameterised surfaces (PTFE, stainless
+ * steel), effective-transparency electrodes and photocathodes with a quantum
+ * efficiency (arXiv:2203.14354, Sec. 2.1-2.2, Table 2, Sec. 3, Appendix).
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (LXO_OK) or a negative lxo_status; no exception crosses the
+ *    ABI.  lxo_last_error(ctx) returns a message owned by the context, valid
+ *    until the next call on that context.
+ *  - "host" pointers are read during the call and stay owned by the caller.
+ *    "device" pointers are CUDA device memory of the context's device, owned
+ *    by the caller, and must stay valid until the work queued on `stream`
+ *    completes.  Geometry, BVH and scratch memory are owned by the context.
+ *  - Calls that take `stream` (a cudaStream_t; NULL = the legacy default
+ *    stream) are asynchronous.  Faults detected inside a kernel (traversal
+ *    stack overflow, channel out of range) set a device error word that
+ *    lxo_sync() reads back and reports as LXO_ERR_DEVICE.
+ *  - Result tallies ACCUMULATE: the caller zeroes them.  Photon p's random
+ *    stream depends only on (seed, p), so splitting a run into several calls
+ *    with disjoint photon_id_base ranges adds up to the same tallies.
+ *
+ * Units: mm, ns.  Speed of light 299.792458 mm/ns; a photon moves at c/n of
+ * the medium it is in.
+ *
+ * Random numbers (identical in every implementation of this method): photon p
+ * uses Philox4x32-10 (Salmon et al., SC'11) with key = (seed low 32 bits, seed
+ * high 32 bits) and counter = (p low, p high, step, draw).  A 32-bit output x
+ * maps to the uniform ((x >> 9) + 0.5) * 2^-23, never 0 or 1.  Source
+ * sampling uses step = 0xFFFFFFFF.  In step s, draw 0 gives
+ * u0 -> absorption distance -L_abs ln u0, u1 -> Rayleigh distance
+ * -L_ray ln u1, u2 -> first surface decision, u3 -> second surface decision;
+ * draw 1 (and 2, 3, ... for Rayleigh rejection tries) gives new directions.
+ */
+#ifndef LXO_H
+#define LXO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lxo_status;
+enum {
+    LXO_OK = 0,
+    LXO_ERR_ARG = -1,     /* invalid argument (message says which) */
+    LXO_ERR_CUDA = -2,    /* a CUDA runtime call failed */
+    LXO_ERR_STATE = -3,   /* call made in the wrong order (e.g. propagate before build_bvh) */
+    LXO_ERR_DEVICE = -4,  /* a kernel reported a fault through the device error word */
+    LXO_ERR_NOMEM = -5    /* host or device allocation failed */
+};
+
+typedef struct lxo_ctx lxo_ctx;
+
+/* ---- tables (Table 2 of the paper; Sec. 2.2 surface models) ---------- */
+
+/* Bulk optical medium.  abs_len_mm / rayleigh_len_mm: mean free paths of
+ * absorption and Rayleigh scattering (Table 2); +inf (or <= 0) = none. */
+typedef struct {
+    float n;
+    float abs_len_mm;
+    float rayleigh_len_mm;
+} lxo_material;
+
+/* surface model types */
+enum {
+    LXO_SURF_ABSORBER = 0,      /* absorbs every photon (PMT cap, Sec. 2.1) */
+    LXO_SURF_REFLECTOR = 1,     /* R_total independent of angle; of the reflected photons a fraction
+                                   spec_frac is specular, the rest Lambertian (Sec. 2.2) */
+    LXO_SURF_PHOTOCATHODE = 2,  /* photosensitive area: counts towards LCE; detected with probability qe */
+    LXO_SURF_ELECTRODE_T = 3    /* thin electrode of effective transparency T (Geant4 model, Sec. 2.1):
+                                   passes straight through with probability T, else hits a wire that
+                                   reflects with wire_reflectivity (specular fraction wire_spec_frac) */
+};
+
+typedef struct {
+    int32_t type;
+    float reflectivity;       /* REFLECTOR: R_total */
+    float spec_frac;          /* REFLECTOR: specular share of reflections, R_spec / (R_spec + R_diff) */
+    float qe;                 /* PHOTOCATHODE */
+    float transparency;       /* ELECTRODE_T */
+    float wire_reflectivity;  /* ELECTRODE_T */
+    float wire_spec_frac;     /* ELECTRODE_T */
+} lxo_surface;
+
+/* PMT table entry (metadata: array 0 = bottom, 1 = top; photocathode centre) */
+typedef struct {
+    int32_t channel;
+    int32_t array;
+    float center[3];
+} lxo_pmt;
+
+/* limits of the tables */
+#define LXO_MAX_MATERIALS 16
+#define LXO_MAX_SURFACES 48
+#define LXO_SURF_NONE 0xFFFFu   /* bare dielectric boundary: Fresnel from the two indices */
+#define LXO_NO_HIT 0xFFFFFFFFu
+
+/* ---- sources (Sec. 3: uniform in the active volume, or point sources;
+ *      isotropic, random linear polarisation, start time t0) ---------- */
+enum {
+    LXO_SRC_VOLUME_POLYGON = 0, /* uniform in an extruded regular polygon: n_sides (0 = circle),
+                                   circumradius `radius`, vertex 0 at angle `phase`, z in [z_min, z_max] */
+    LXO_SRC_POINT = 1,          /* at `center` */
+    LXO_SRC_SEGMENT = 2,        /* uniform on the segment center -> p1 */
+    LXO_SRC_BALL = 3,           /* uniform in the ball (center, radius) */
+    LXO_SRC_EXPLICIT = 4        /* per-photon device arrays pos/dir/pol [n*3] (photon i = id - base) */
+};
+
+typedef struct {
+    int32_t kind;
+    int32_t medium;       /* material index the photons start in */
+    int32_t n_sides;
+    int32_t reserved;
+    float radius, phase, z_min, z_max;
+    float center[3];
+    float p1[3];
+    float t0;             /* ns */
+    const float* pos;     /* EXPLICIT only, device [n*3] */
+    const float* dir;     /* EXPLICIT only, device [n*3], unit */
+    const float* pol;     /* EXPLICIT only, device [n*3], unit, made perpendicular to dir */
+} lxo_source;
+
+/* ---- run parameters and results --------------------------------------- */
+typedef struct {
+    uint64_t seed;
+    uint32_t max_steps;   /* interactions per photon before it is cut as TRUNCATED (0 = 10000) */
+    uint32_t n_tbins;     /* arrival-time bins per channel; bin n_tbins is the overflow */
+    float tbin_ns;        /* bin width (> 0) */
+    uint32_t flags;       /* LXO_FLAG_* */
+} lxo_run_params;
+
+/* run flags */
+#define LXO_FLAG_STATS 1u  /* count traversal work into lxo_results.stats (a separate kernel build) */
+
+/* fate codes (per photon) */
+enum {
+    LXO_FATE_DETECTED = 0,   /* reached a photocathode and passed the QE draw */
+    LXO_FATE_QE_FAIL = 1,    /* reached a photocathode, not detected */
+    LXO_FATE_BULK_ABS = 2,   /* absorbed in a medium */
+    LXO_FATE_SURF_ABS = 3,   /* absorbed by a surface (reflector, cap, electrode wire) */
+    LXO_FATE_ESCAPED = 4,    /* left the geometry (a leak: no surface ahead, no bulk process) */
+    LXO_FATE_TRUNCATED = 5,  /* max_steps reached */
+    LXO_FATE_GEOM_ERR = 6    /* inconsistent medium at a boundary or bad channel */
+};
+/* fates[] layout: [0..6] count per fate code, [7] total steps of all photons,
+ * [8 + m] bulk absorptions in material m, [8 + M + s] absorptions on surface s
+ * (M materials, S surfaces as set) -- the loss bookkeeping of Table 6. */
+#define LXO_FATES_FIXED 8
+
+typedef struct {
+    uint32_t* lce;               /* device [P]: photocathode arrivals (light collection, Sec. 3) */
+    uint32_t* det;               /* device [P]: detected after QE */
+    uint32_t* hist;              /* device [P*(n_tbins+1)]: detected arrival-time histogram (row = channel) */
+    unsigned long long* fates;   /* device [8+M+S] */
+    uint32_t* ph_fate;           /* optional device [n]: fate code per photon */
+    int32_t* ph_detail;          /* optional device [n]: channel / material / surface / triangle */
+    uint32_t* ph_steps;          /* optional device [n] */
+    float* ph_time;              /* optional device [n]: time at the end, ns */
+    unsigned long long* stats;   /* device [4] with LXO_FLAG_STATS: steps, BVH nodes visited,
+                                    leaves visited, triangles tested (accumulated) */
+} lxo_results;
+
+typedef struct {
+    uint32_t n_tris, n_nodes, n_leaves, max_depth;
+    uint64_t node_bytes, tri_bytes;
+    double build_seconds, sah_cost;
+} lxo_bvh_info;
+
+typedef struct {
+    uint32_t leaf_size;   /* max triangles per leaf, 1..8 (0 = 4) */
+    uint32_t sah_bins;    /* bins per axis, 4..64 (0 = 16) */
+    uint32_t n_threads;   /* host threads (0 = all cores) */
+    uint32_t reserved;
+} lxo_bvh_params;
+
+/* ---- entry points ------------------------------------------------------ */
+
+/* Creates a context on CUDA device `cuda_device` (allocates its scratch). */
+lxo_status lxo_create(lxo_ctx** out, int cuda_device);
+void lxo_destroy(lxo_ctx* ctx);
+const char* lxo_last_error(const lxo_ctx* ctx);
+
+/* Detector mesh (Sec. 2.1: the detector as triangles, each boundary with the
+ * materials on its two sides, a surface model and, for photocathodes, a PMT
+ * channel).  Host arrays: verts [nv*3] mm; tris [nt*3] vertex indices;
+ * mat_inner/mat_outer [nt] material on the side the geometric normal
+ * (v1-v0)x(v2-v0) points away from / towards; surface [nt] surface index or
+ * LXO_SURF_NONE; channel [nt] PMT channel of photocathode triangles, -1
+ * elsewhere.  Copied; invalidates a previous BVH. */
+lxo_status lxo_load_mesh(lxo_ctx* ctx, const float* verts, uint32_t nv, const uint32_t* tris, uint32_t nt,
+                         const uint8_t* mat_inner, const uint8_t* mat_outer, const uint16_t* surface,
+                         const int32_t* channel);
+/* Material table (Table 2).  Host array of n <= LXO_MAX_MATERIALS. */
+lxo_status lxo_set_materials(lxo_ctx* ctx, const lxo_material* m, uint32_t n);
+/* Surface table (Sec. 2.2).  Host array of n <= LXO_MAX_SURFACES. */
+lxo_status lxo_set_surfaces(lxo_ctx* ctx, const lxo_surface* s, uint32_t n);
+/* PMT table: n channels (the P of every per-channel tally). */
+lxo_status lxo_set_pmts(lxo_ctx* ctx, const lxo_pmt* p, uint32_t n);
+
+/* Builds the bounding-volume hierarchy on the host (binned SAH, all cores)
+ * and uploads nodes and triangles to the device.  params may be NULL.
+ * info (host, may be NULL) receives sizes and the build time. */
+lxo_status lxo_build_bvh(lxo_ctx* ctx, const lxo_bvh_params* params, lxo_bvh_info* info);
+
+/* Closest hit for n rays (device arrays): smallest t in (0, tmax] over all
+ * triangles except skip[i] (LXO_NO_HIT = none), ties to the smallest
+ * triangle index; float32 watertight test (Woop, Benthin & Wald, JCGT 2013).
+ * org/dir [n*3]; skip, tmax may be NULL (none / +inf).  Writes hit [n]
+ * (LXO_NO_HIT on miss) and t [n] (+inf on miss). */
+lxo_status lxo_trace_rays(lxo_ctx* ctx, const float* org, const float* dir, const uint32_t* skip,
+                          const float* tmax, uint32_t n, uint32_t* hit, float* t, void* stream);
+
+/* The first state of photons base .. base+n-1 from a source: device arrays
+ * pos, dir, pol [n*3] (float). */
+lxo_status lxo_sample_source(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
+                             uint64_t seed, float* pos, float* dir, float* pol, void* stream);
+
+/* Propagates photons base .. base+n-1 to their fates and accumulates the
+ * tallies into `out` (device buffers, caller-owned, zeroed by the caller).
+ * Requires mesh, materials, surfaces, PMTs and BVH. */
+lxo_status lxo_propagate(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
+                         const lxo_run_params* params, const lxo_results* out, void* stream);
+
+/* The same with HOST result buffers (lce, det, hist, fates; the per-photon
+ * arrays must be NULL): zeroes context-owned device tallies, propagates,
+ * copies the tallies back and ADDS them to the host arrays.  Synchronous. */
+lxo_status lxo_propagate_host(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
+                              const lxo_run_params* params, const lxo_results* host_out, void* stream);
+
+/* Waits for `stream` and reports a device-side fault recorded since the last
+ * lxo_sync (then clears it). */
+lxo_status lxo_sync(lxo_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LXO_H */

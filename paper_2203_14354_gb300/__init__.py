@@ -1,2 +1,18 @@
-"""GB300-native Monte Carlo propagation of LXe scintillation photons through a
-triangle-mesh detector (optical simulation of a DARWIN-like dual-phase TPC)."""
+"""GB300-native Monte Carlo propagation of liquid-xenon scintillation photons
+through a triangle-mesh detector (the optical simulation of a DARWIN-like
+dual-phase TPC, arXiv:2203.14354).
+
+* ``geometry``  -- procedural detector meshes, optical tables, photon sources
+* ``tracker``   -- ``Tracker``: the CUDA library behind the C ABI of include/lxo.h
+* ``_capi``     -- ctypes binding with the C names
+"""
+from . import geometry  # noqa: F401
+
+__all__ = ["geometry", "Tracker"]
+
+
+def __getattr__(name):
+    if name == "Tracker":
+        from .tracker import Tracker
+        return Tracker
+    raise AttributeError(name)

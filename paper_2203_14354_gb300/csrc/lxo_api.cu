@@ -1,0 +1,465 @@
+// C ABI of the photon tracker (declared in include/lxo.h): context, mesh and
+// table upload, BVH build + upload, and the launches.  Host code only; the
+// kernels are in lxo_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lxo_internal.h"
+
+struct lxo_ctx {
+    int device = 0;
+    std::string err;
+    // host mesh
+    uint32_t nt = 0;
+    std::vector<float> tri_v;      // [nt*9]
+    std::vector<uint32_t> attr;    // [nt]
+    std::vector<int32_t> chan;     // [nt]
+    float max_abs = 1.0f;
+    bool have_mesh = false, have_bvh = false, validated = false;
+    std::vector<lxo_material> mats;
+    std::vector<lxo_surface> surfs;
+    std::vector<lxo_pmt> pmts;
+    // device
+    float4* d_nodes = nullptr;
+    float4* d_tris = nullptr;
+    unsigned long long* d_queue = nullptr;  // scratch: work-queue head
+    int* d_err = nullptr;                   // scratch: device error word
+    void* d_tally = nullptr;                // tallies of lxo_propagate_host
+    size_t tally_bytes = 0;
+    lxo_bvh_info info{};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+lxo_status fail(lxo_ctx* c, lxo_status code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+lxo_status cuda_fail(lxo_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, LXO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+void free_device_geometry(lxo_ctx* c)
+{
+    if (c->d_nodes) cudaFree(c->d_nodes);
+    if (c->d_tris) cudaFree(c->d_tris);
+    c->d_nodes = nullptr;
+    c->d_tris = nullptr;
+    c->have_bvh = false;
+}
+
+lxo_status validate(lxo_ctx* c)
+{
+    if (c->validated) return LXO_OK;
+    if (!c->have_mesh) return fail(c, LXO_ERR_STATE, "no mesh loaded");
+    if (c->mats.empty()) return fail(c, LXO_ERR_STATE, "no materials set");
+    if (c->pmts.empty()) return fail(c, LXO_ERR_STATE, "no PMT table set");
+    if (!c->have_bvh) return fail(c, LXO_ERR_STATE, "BVH not built");
+    const uint32_t M = (uint32_t)c->mats.size(), S = (uint32_t)c->surfs.size(), P = (uint32_t)c->pmts.size();
+    for (uint32_t i = 0; i < c->nt; ++i) {
+        const uint32_t a = c->attr[i];
+        const uint32_t mi = a & 0xFF, mo = (a >> 8) & 0xFF, sf = a >> 16;
+        if (mi >= M || mo >= M)
+            return fail(c, LXO_ERR_ARG, "triangle %u: material index (%u, %u) >= %u materials", i, mi, mo, M);
+        if (sf != LXO_SURF_NONE && sf >= S)
+            return fail(c, LXO_ERR_ARG, "triangle %u: surface %u >= %u surfaces", i, sf, S);
+        if (sf != LXO_SURF_NONE && c->surfs[sf].type == LXO_SURF_PHOTOCATHODE &&
+            (c->chan[i] < 0 || (uint32_t)c->chan[i] >= P))
+            return fail(c, LXO_ERR_ARG, "triangle %u: photocathode channel %d outside [0, %u)", i, c->chan[i], P);
+    }
+    c->validated = true;
+    return LXO_OK;
+}
+
+lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, const lxo_run_params* rp,
+                       lxo::PropParams* p)
+{
+    if (!src) return fail(c, LXO_ERR_ARG, "source is NULL");
+    memset(p, 0, sizeof *p);
+    const int M = (int)c->mats.size(), S = (int)c->surfs.size();
+    p->sc.nodes = c->d_nodes;
+    p->sc.tris = c->d_tris;
+    p->sc.n_tris = c->nt;
+    for (int m = 0; m < M; ++m) {
+        const lxo_material& x = c->mats[m];
+        p->mat[m].n = x.n;
+        p->mat[m].n_over_c = (float)((double)x.n / 299.792458);
+        p->mat[m].abs_len = (x.abs_len_mm > 0.0f && std::isfinite(x.abs_len_mm)) ? x.abs_len_mm : INFINITY;
+        p->mat[m].ray_len =
+            (x.rayleigh_len_mm > 0.0f && std::isfinite(x.rayleigh_len_mm)) ? x.rayleigh_len_mm : INFINITY;
+    }
+    for (int s = 0; s < S; ++s) {
+        const lxo_surface& x = c->surfs[s];
+        p->surf[s] = lxo::DevSurface{x.type, x.reflectivity, x.spec_frac, x.qe, x.transparency,
+                                     x.wire_reflectivity, x.wire_spec_frac};
+    }
+    p->n_mat = M;
+    p->n_surf = S;
+    p->n_chan = (int)c->pmts.size();
+    p->n_fates = LXO_FATES_FIXED + M + S;
+    if (src->kind < LXO_SRC_VOLUME_POLYGON || src->kind > LXO_SRC_EXPLICIT)
+        return fail(c, LXO_ERR_ARG, "unknown source kind %d", src->kind);
+    if (src->medium < 0 || src->medium >= M)
+        return fail(c, LXO_ERR_ARG, "source medium %d outside [0, %d)", src->medium, M);
+    if (src->kind == LXO_SRC_VOLUME_POLYGON && (src->n_sides < 0 || src->n_sides > lxo::kMaxPolySides ||
+                                                 src->n_sides == 1 || src->n_sides == 2))
+        return fail(c, LXO_ERR_ARG, "polygon source: n_sides %d not in {0, 3..%d}", src->n_sides,
+                    lxo::kMaxPolySides);
+    if (src->kind == LXO_SRC_EXPLICIT && (!src->pos || !src->dir || !src->pol))
+        return fail(c, LXO_ERR_ARG, "explicit source needs pos, dir and pol device arrays");
+    lxo::SourceDev& sd = p->src;
+    sd.kind = src->kind;
+    sd.medium = src->medium;
+    sd.n_sides = src->n_sides;
+    sd.radius = src->radius;
+    sd.z_min = src->z_min;
+    sd.z_max = src->z_max;
+    sd.t0 = src->t0;
+    for (int a = 0; a < 3; ++a) {
+        sd.center[a] = src->center[a];
+        sd.p1[a] = src->p1[a];
+    }
+    if (src->kind == LXO_SRC_VOLUME_POLYGON && src->n_sides > 0) {
+        const double pi = 3.141592653589793;
+        sd.apothem = (float)((double)src->radius * cos(pi / src->n_sides));
+        for (int k = 0; k < src->n_sides; ++k) {
+            const double a = (double)src->phase + 2.0 * pi * (k + 0.5) / src->n_sides;
+            sd.side_cos[k] = (float)cos(a);
+            sd.side_sin[k] = (float)sin(a);
+        }
+    }
+    sd.pos = src->pos;
+    sd.dir = src->dir;
+    sd.pol = src->pol;
+    p->n = n;
+    p->base = base;
+    if (rp) {
+        p->seed = rp->seed;
+        p->max_steps = rp->max_steps ? rp->max_steps : 10000u;
+        p->n_tbins = rp->n_tbins;
+        p->tbin = rp->tbin_ns;
+        p->flags = rp->flags;
+        if (!(rp->tbin_ns > 0.0f)) return fail(c, LXO_ERR_ARG, "tbin_ns must be > 0");
+    }
+    p->queue = c->d_queue;
+    p->err = c->d_err;
+    return LXO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lxo_status lxo_create(lxo_ctx** out, int cuda_device)
+{
+    if (!out) return LXO_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return LXO_ERR_CUDA;
+    if (cuda_device < 0 || cuda_device >= n) return LXO_ERR_ARG;
+    lxo_ctx* c = new (std::nothrow) lxo_ctx();
+    if (!c) return LXO_ERR_NOMEM;
+    c->device = cuda_device;
+    DeviceGuard g(cuda_device);
+    if (cudaMalloc(&c->d_queue, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        lxo_destroy(c);
+        return LXO_ERR_CUDA;
+    }
+    *out = c;
+    return LXO_OK;
+}
+
+void lxo_destroy(lxo_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard g(c->device);
+    free_device_geometry(c);
+    if (c->d_queue) cudaFree(c->d_queue);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->d_tally) cudaFree(c->d_tally);
+    delete c;
+}
+
+const char* lxo_last_error(const lxo_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+lxo_status lxo_load_mesh(lxo_ctx* c, const float* verts, uint32_t nv, const uint32_t* tris, uint32_t nt,
+                         const uint8_t* mat_inner, const uint8_t* mat_outer, const uint16_t* surface,
+                         const int32_t* channel)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!verts || !tris || !mat_inner || !mat_outer || !surface || !channel)
+        return fail(c, LXO_ERR_ARG, "load_mesh: NULL array");
+    if (nt == 0 || nt >= (1u << 28)) return fail(c, LXO_ERR_ARG, "load_mesh: %u triangles not in [1, 2^28)", nt);
+    for (uint64_t i = 0; i < 3ull * nv; ++i)
+        if (!std::isfinite(verts[i])) return fail(c, LXO_ERR_ARG, "load_mesh: vertex %llu not finite",
+                                                  (unsigned long long)(i / 3));
+    try {
+        c->tri_v.resize(9ull * nt);
+        c->attr.resize(nt);
+        c->chan.resize(nt);
+    } catch (...) {
+        return fail(c, LXO_ERR_NOMEM, "load_mesh: out of host memory");
+    }
+    float mx = 1.0f;
+    for (uint64_t i = 0; i < nt; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            const uint32_t v = tris[3 * i + j];
+            if (v >= nv) return fail(c, LXO_ERR_ARG, "load_mesh: triangle %llu vertex index %u >= %u",
+                                     (unsigned long long)i, v, nv);
+            for (int a = 0; a < 3; ++a) {
+                const float x = verts[3ull * v + a];
+                c->tri_v[9 * i + 3 * j + a] = x;
+                mx = std::max(mx, std::fabs(x));
+            }
+        }
+        c->attr[i] = (uint32_t)mat_inner[i] | ((uint32_t)mat_outer[i] << 8) | ((uint32_t)surface[i] << 16);
+        c->chan[i] = channel[i];
+    }
+    c->nt = nt;
+    c->max_abs = mx;
+    c->have_mesh = true;
+    c->validated = false;
+    DeviceGuard g(c->device);
+    free_device_geometry(c);
+    return LXO_OK;
+}
+
+lxo_status lxo_set_materials(lxo_ctx* c, const lxo_material* m, uint32_t n)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!m || n == 0 || n > LXO_MAX_MATERIALS)
+        return fail(c, LXO_ERR_ARG, "set_materials: need 1..%d materials", LXO_MAX_MATERIALS);
+    for (uint32_t i = 0; i < n; ++i)
+        if (!(m[i].n > 0.0f) || std::isnan(m[i].abs_len_mm) || std::isnan(m[i].rayleigh_len_mm))
+            return fail(c, LXO_ERR_ARG, "set_materials: material %u invalid (n must be > 0, lengths not NaN)", i);
+    c->mats.assign(m, m + n);
+    c->validated = false;
+    return LXO_OK;
+}
+
+lxo_status lxo_set_surfaces(lxo_ctx* c, const lxo_surface* s, uint32_t n)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (n > LXO_MAX_SURFACES || (n && !s)) return fail(c, LXO_ERR_ARG, "set_surfaces: need 0..%d surfaces",
+                                                       LXO_MAX_SURFACES);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (s[i].type < LXO_SURF_ABSORBER || s[i].type > LXO_SURF_ELECTRODE_T)
+            return fail(c, LXO_ERR_ARG, "set_surfaces: surface %u has unknown type %d", i, s[i].type);
+        const float v[6] = {s[i].reflectivity, s[i].spec_frac, s[i].qe, s[i].transparency, s[i].wire_reflectivity,
+                            s[i].wire_spec_frac};
+        for (float x : v)
+            if (!(x >= 0.0f && x <= 1.0f))
+                return fail(c, LXO_ERR_ARG, "set_surfaces: surface %u has a probability outside [0, 1]", i);
+    }
+    c->surfs.assign(s, s + n);
+    c->validated = false;
+    return LXO_OK;
+}
+
+lxo_status lxo_set_pmts(lxo_ctx* c, const lxo_pmt* p, uint32_t n)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!p || n == 0) return fail(c, LXO_ERR_ARG, "set_pmts: need at least one channel");
+    c->pmts.assign(p, p + n);
+    c->validated = false;
+    return LXO_OK;
+}
+
+lxo_status lxo_build_bvh(lxo_ctx* c, const lxo_bvh_params* bp, lxo_bvh_info* info)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!c->have_mesh) return fail(c, LXO_ERR_STATE, "build_bvh: no mesh loaded");
+    lxo_bvh_params q{};
+    if (bp) q = *bp;
+    lxo::BvhHost b;
+    char msg[256] = {0};
+    // widen boxes far beyond the float rounding of the slab test
+    const float expand = std::ldexp(c->max_abs, -19);
+    if (lxo::build_bvh(c->tri_v.data(), c->nt, q.leaf_size, q.sah_bins, q.n_threads, expand, &b, msg, sizeof msg))
+        return fail(c, LXO_ERR_NOMEM, "%s", msg);
+    // attributes of each record
+    for (uint32_t k = 0; k < b.n_records; ++k) {
+        float4& r2 = b.tris[3ull * k + 2];
+        uint32_t id;
+        memcpy(&id, &r2.y, 4);
+        const uint32_t a = c->attr[id];
+        const int32_t ch = c->chan[id];
+        memcpy(&r2.z, &a, 4);
+        memcpy(&r2.w, &ch, 4);
+    }
+    DeviceGuard g(c->device);
+    free_device_geometry(c);
+    const size_t nb = sizeof(float4) * 4ull * b.n_nodes, tb = sizeof(float4) * 3ull * b.n_records;
+    cudaError_t e = cudaMalloc(&c->d_nodes, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tris, tb);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_nodes, b.nodes, nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_tris, b.tris, tb, cudaMemcpyHostToDevice);
+    lxo::free_bvh(&b);
+    if (e != cudaSuccess) {
+        free_device_geometry(c);
+        return cuda_fail(c, e, "build_bvh: upload");
+    }
+    c->info.n_tris = c->nt;
+    c->info.n_nodes = b.n_nodes;
+    c->info.n_leaves = b.n_leaves;
+    c->info.max_depth = b.max_depth;
+    c->info.node_bytes = nb;
+    c->info.tri_bytes = tb;
+    c->info.build_seconds = b.build_seconds;
+    c->info.sah_cost = b.sah_cost;
+    if (info) *info = c->info;
+    c->have_bvh = true;
+    c->validated = false;
+    if (b.max_depth >= (uint32_t)lxo::kStackSize)
+        return fail(c, LXO_ERR_ARG, "build_bvh: depth %u exceeds the traversal stack", b.max_depth);
+    return LXO_OK;
+}
+
+lxo_status lxo_trace_rays(lxo_ctx* c, const float* org, const float* dir, const uint32_t* skip, const float* tmax,
+                          uint32_t n, uint32_t* hit, float* t, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!c->have_bvh) return fail(c, LXO_ERR_STATE, "trace_rays: BVH not built");
+    if (n == 0) return LXO_OK;
+    if (!org || !dir || !hit || !t) return fail(c, LXO_ERR_ARG, "trace_rays: NULL array");
+    DeviceGuard g(c->device);
+    lxo::Scene sc{c->d_nodes, c->d_tris, c->nt};
+    CK(lxo::launch_trace(sc, org, dir, skip, tmax, n, hit, t, c->d_err, (cudaStream_t)stream), "trace_rays");
+    return LXO_OK;
+}
+
+lxo_status lxo_sample_source(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, uint64_t seed,
+                             float* pos, float* dir, float* pol, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (c->mats.empty()) return fail(c, LXO_ERR_STATE, "sample_source: no materials set");
+    if (n == 0) return LXO_OK;
+    if (!pos || !dir || !pol) return fail(c, LXO_ERR_ARG, "sample_source: NULL array");
+    lxo::PropParams p;
+    lxo_run_params rp{seed, 1, 0, 1.0f, 0};
+    lxo_status s = fill_params(c, src, n, base, &rp, &p);
+    if (s) return s;
+    DeviceGuard g(c->device);
+    CK(lxo::launch_sample_source(p, pos, dir, pol, (cudaStream_t)stream), "sample_source");
+    return LXO_OK;
+}
+
+lxo_status lxo_propagate(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, const lxo_run_params* rp,
+                         const lxo_results* out, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    lxo_status s = validate(c);
+    if (s) return s;
+    if (!rp) return fail(c, LXO_ERR_ARG, "propagate: run params are NULL");
+    if (!out || !out->lce || !out->det || !out->hist || !out->fates)
+        return fail(c, LXO_ERR_ARG, "propagate: lce, det, hist and fates buffers are required");
+    if ((rp->flags & LXO_FLAG_STATS) && !out->stats)
+        return fail(c, LXO_ERR_ARG, "propagate: LXO_FLAG_STATS needs the stats buffer");
+    if (n == 0) return LXO_OK;
+    lxo::PropParams p;
+    s = fill_params(c, src, n, base, rp, &p);
+    if (s) return s;
+    p.out = *out;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long), st), "propagate: reset queue");
+    CK(lxo::launch_propagate(p, c->device, st), "propagate: launch");
+    return LXO_OK;
+}
+
+lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base,
+                              const lxo_run_params* rp, const lxo_results* host_out, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    lxo_status s = validate(c);
+    if (s) return s;
+    if (!rp) return fail(c, LXO_ERR_ARG, "propagate_host: run params are NULL");
+    if (!host_out || !host_out->lce || !host_out->det || !host_out->hist || !host_out->fates)
+        return fail(c, LXO_ERR_ARG, "propagate_host: lce, det, hist and fates buffers are required");
+    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->stats)
+        return fail(c, LXO_ERR_ARG, "propagate_host: per-photon outputs and stats are device-only");
+    if (rp->flags & LXO_FLAG_STATS) return fail(c, LXO_ERR_ARG, "propagate_host: LXO_FLAG_STATS not supported");
+    const size_t P = c->pmts.size(), B = (size_t)rp->n_tbins + 1;
+    const size_t NF = LXO_FATES_FIXED + c->mats.size() + c->surfs.size();
+    const size_t bytes = 8 * NF + 4 * (2 * P + P * B);
+    DeviceGuard g(c->device);
+    if (c->tally_bytes < bytes) {
+        if (c->d_tally) cudaFree(c->d_tally);
+        c->d_tally = nullptr;
+        c->tally_bytes = 0;
+        CK(cudaMalloc(&c->d_tally, bytes), "propagate_host: tallies");
+        c->tally_bytes = bytes;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    lxo_results d{};
+    d.fates = (unsigned long long*)c->d_tally;
+    d.lce = (uint32_t*)(d.fates + NF);
+    d.det = d.lce + P;
+    d.hist = d.det + P;
+    CK(cudaMemsetAsync(c->d_tally, 0, bytes, st), "propagate_host: zero tallies");
+    s = lxo_propagate(c, src, n, base, rp, &d, stream);
+    if (s) return s;
+    std::vector<unsigned long long> hf(NF);
+    std::vector<uint32_t> hu(2 * P + P * B);
+    CK(cudaMemcpyAsync(hf.data(), d.fates, 8 * NF, cudaMemcpyDeviceToHost, st), "propagate_host: copy fates");
+    CK(cudaMemcpyAsync(hu.data(), d.lce, 4 * hu.size(), cudaMemcpyDeviceToHost, st), "propagate_host: copy tallies");
+    s = lxo_sync(c, stream);
+    if (s) return s;
+    for (size_t i = 0; i < NF; ++i) host_out->fates[i] += hf[i];
+    for (size_t i = 0; i < P; ++i) {
+        host_out->lce[i] += hu[i];
+        host_out->det[i] += hu[P + i];
+    }
+    for (size_t i = 0; i < P * B; ++i) host_out->hist[i] += hu[2 * P + i];
+    return LXO_OK;
+}
+
+lxo_status lxo_sync(lxo_ctx* c, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "sync");
+    int h = 0;
+    CK(cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "sync: read error word");
+    if (h) {
+        CK(cudaMemset(c->d_err, 0, sizeof(int)), "sync: clear error word");
+        return fail(c, LXO_ERR_DEVICE, "device fault flags 0x%x (1 = traversal stack, 2 = channel range)", h);
+    }
+    return LXO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,702 @@
+// Device code of the photon tracker (sm_103a).
+//
+//  * k_trace:          one ray per lane, closest hit (the geometry query alone).
+//  * k_sample_source:  first photon state from a source (one photon per lane).
+//  * k_propagate:      persistent kernel; each lane carries one photon from its
+//                      source to its fate (bulk absorption, Rayleigh, Fresnel /
+//                      TIR, reflectors, electrodes, photocathode).  A lane whose
+//                      photon died is refilled from a warp-local chunk of photon
+//                      ids (warp ballot + prefix popcount), chunks come from a
+//                      global atomic work queue: no lane idles while photons
+//                      remain.  Fate tallies live in shared memory per CTA;
+//                      per-channel counts and the time histogram use global
+//                      atomics.
+//
+// Bit-exactness of the closest hit: the triangle test below performs the same
+// IEEE float operations, in the same order, as a plain C implementation of
+// the watertight test (Woop, Benthin & Wald, JCGT 2013); every operation is an
+// explicit round-to-nearest intrinsic so the compiler cannot contract or
+// reorder it.  Boxes are widened at build time and the box test uses a
+// relative slack, so the traversal visits every box that holds a candidate.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lxo_internal.h"
+
+namespace lxo {
+
+#define FULL_MASK 0xFFFFFFFFu
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+struct U4 {
+    float u0, u1, u2, u3;
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float u01(uint32_t x)
+{
+    // ((x >> 9) + 0.5) * 2^-23: exact in float, in [2^-24, 1 - 2^-24]
+    return __fmul_rn(__uint2float_rn(x >> 9) + 0.5f, 1.1920928955078125e-07f);
+}
+
+__device__ __forceinline__ U4 draw4(uint64_t seed, uint64_t pid, uint32_t step, uint32_t draw)
+{
+    uint4 o = philox4x32_10(make_uint4((uint32_t)pid, (uint32_t)(pid >> 32), step, draw),
+                            make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    return U4{u01(o.x), u01(o.y), u01(o.z), u01(o.w)};
+}
+
+// ---------------------------------------------------------------------------
+// small float3 helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b)
+{
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 a) { return rsqrtf(dot(a, a)) * a; }
+
+// orthonormal basis perpendicular to unit n (Duff et al., JCGT 6(1), 2017)
+__device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2)
+{
+    float sgn = copysignf(1.0f, n.z);
+    float a = -1.0f / (sgn + n.z);
+    float b = n.x * n.y * a;
+    t1 = f3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
+    t2 = f3(b, sgn + n.y * n.y * a, -n.y);
+}
+
+// ---------------------------------------------------------------------------
+// watertight ray / triangle test (exact op order, see file header)
+// ---------------------------------------------------------------------------
+struct WRay {
+    float ox, oy, oz;
+    float Sx, Sy, Sz;
+    int kx, ky, kz;
+};
+
+__device__ __forceinline__ float pick(int k, float x, float y, float z) { return k == 0 ? x : (k == 1 ? y : z); }
+
+__device__ __forceinline__ WRay wray_setup(float3 o, float3 d)
+{
+    WRay r;
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax >= ay) ? ((ax >= az) ? 0 : 2) : ((ay >= az) ? 1 : 2);
+    int kx = kz + 1;
+    if (kx == 3) kx = 0;
+    int ky = kx + 1;
+    if (ky == 3) ky = 0;
+    float dkz = pick(kz, d.x, d.y, d.z);
+    if (dkz < 0.0f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    r.Sx = __fdiv_rn(pick(kx, d.x, d.y, d.z), dkz);
+    r.Sy = __fdiv_rn(pick(ky, d.x, d.y, d.z), dkz);
+    r.Sz = __fdiv_rn(1.0f, dkz);
+    r.ox = o.x;
+    r.oy = o.y;
+    r.oz = o.z;
+    return r;
+}
+
+__device__ __forceinline__ bool wray_hit(const WRay& r, float4 a, float4 b, float4 c, float tmax, float& t_out)
+{
+    // vertices v0 = a.xyz, v1 = (a.w, b.x, b.y), v2 = (b.z, b.w, c.x)
+    const float A0 = __fsub_rn(a.x, r.ox), A1 = __fsub_rn(a.y, r.oy), A2 = __fsub_rn(a.z, r.oz);
+    const float B0 = __fsub_rn(a.w, r.ox), B1 = __fsub_rn(b.x, r.oy), B2 = __fsub_rn(b.y, r.oz);
+    const float C0 = __fsub_rn(b.z, r.ox), C1 = __fsub_rn(b.w, r.oy), C2 = __fsub_rn(c.x, r.oz);
+    const float Akz = pick(r.kz, A0, A1, A2), Bkz = pick(r.kz, B0, B1, B2), Ckz = pick(r.kz, C0, C1, C2);
+    const float Ax = __fsub_rn(pick(r.kx, A0, A1, A2), __fmul_rn(r.Sx, Akz));
+    const float Ay = __fsub_rn(pick(r.ky, A0, A1, A2), __fmul_rn(r.Sy, Akz));
+    const float Bx = __fsub_rn(pick(r.kx, B0, B1, B2), __fmul_rn(r.Sx, Bkz));
+    const float By = __fsub_rn(pick(r.ky, B0, B1, B2), __fmul_rn(r.Sy, Bkz));
+    const float Cx = __fsub_rn(pick(r.kx, C0, C1, C2), __fmul_rn(r.Sx, Ckz));
+    const float Cy = __fsub_rn(pick(r.ky, C0, C1, C2), __fmul_rn(r.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = __double2float_rn(__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx)));
+        V = __double2float_rn(__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx)));
+        W = __double2float_rn(__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax)));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.0f) return false;
+    const float Az = __fmul_rn(r.Sz, Akz), Bz = __fmul_rn(r.Sz, Bkz), Cz = __fmul_rn(r.Sz, Ckz);
+    const float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Az), __fmul_rn(V, Bz)), __fmul_rn(W, Cz));
+    const float t = __fdiv_rn(T, det);
+    if (!(t > 0.0f) || !(t <= tmax)) return false;
+    t_out = t;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// BVH traversal: closest hit with t in (0, tmax], skipping one triangle,
+// ties to the smallest triangle id.
+// ---------------------------------------------------------------------------
+constexpr float kBoxSlack = 1.0f + 1.0f / 65536.0f;
+
+struct Hit {
+    uint32_t id;   // triangle id (LXO_NO_HIT on miss)
+    uint32_t rec;  // record index in leaf order
+    float t;
+};
+
+__device__ __forceinline__ float safe_inv(float d)
+{
+    return __frcp_rn(fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d);
+}
+
+struct Counters {
+    uint32_t nodes, leaves, tris;
+};
+
+template <bool kStats>
+__device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, float tmax, int* err, Counters& cnt)
+{
+    const WRay wr = wray_setup(o, d);
+    const float ix = safe_inv(d.x), iy = safe_inv(d.y), iz = safe_inv(d.z);
+    const float oix = o.x * ix, oiy = o.y * iy, oiz = o.z * iz;
+    uint32_t best = LXO_NO_HIT, best_rec = 0;
+    float bt = tmax;
+    int stack[kStackSize];
+    int sp = 0;
+    int ref = 0;
+    while (true) {
+        if (ref >= 0) {
+            if (kStats) cnt.nodes++;
+            const float4* nd = sc.nodes + 4 * (size_t)ref;
+            const float4 nx = __ldg(nd + 0), ny = __ldg(nd + 1), nz = __ldg(nd + 2);
+            const int4 cr = __ldg(reinterpret_cast<const int4*>(nd + 3));
+            const float lim = bt * kBoxSlack;
+            const float ax0 = fmaf(nx.x, ix, -oix), ax1 = fmaf(nx.y, ix, -oix);
+            const float ay0 = fmaf(ny.x, iy, -oiy), ay1 = fmaf(ny.y, iy, -oiy);
+            const float az0 = fmaf(nz.x, iz, -oiz), az1 = fmaf(nz.y, iz, -oiz);
+            const float bx0 = fmaf(nx.z, ix, -oix), bx1 = fmaf(nx.w, ix, -oix);
+            const float by0 = fmaf(ny.z, iy, -oiy), by1 = fmaf(ny.w, iy, -oiy);
+            const float bz0 = fmaf(nz.z, iz, -oiz), bz1 = fmaf(nz.w, iz, -oiz);
+            const float an = fmaxf(fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)), fmaxf(fminf(az0, az1), 0.0f));
+            const float af = fminf(fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)), fminf(fmaxf(az0, az1), lim));
+            const float bn = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), 0.0f));
+            const float bf = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), lim));
+            const bool ha = an <= af;
+            const bool hb = (bn <= bf) && (cr.y != kEmptyChild);
+            if (ha && hb) {
+                const bool a_first = an <= bn;
+                const int nearr = a_first ? cr.x : cr.y;
+                const int farr = a_first ? cr.y : cr.x;
+                if (sp >= kStackSize) {
+                    atomicOr(err, kErrStack);
+                    break;
+                }
+                stack[sp++] = farr;
+                ref = nearr;
+            } else if (ha) {
+                ref = cr.x;
+            } else if (hb) {
+                ref = cr.y;
+            } else {
+                if (sp == 0) break;
+                ref = stack[--sp];
+            }
+        } else {
+            const uint32_t enc = ~(uint32_t)ref;
+            const uint32_t first = enc >> 3, count = (enc & 7u) + 1u;
+            if (kStats) {
+                cnt.leaves++;
+                cnt.tris += count;
+            }
+            for (uint32_t k = 0; k < count; ++k) {
+                const float4* tr = sc.tris + 3 * (size_t)(first + k);
+                const float4 a = __ldg(tr + 0), b = __ldg(tr + 1), c = __ldg(tr + 2);
+                const uint32_t id = __float_as_uint(c.y);
+                if (id == skip) continue;
+                float t;
+                if (wray_hit(wr, a, b, c, bt, t)) {
+                    if (t < bt || (t == bt && (best == LXO_NO_HIT || id < best))) {
+                        bt = t;
+                        best = id;
+                        best_rec = first + k;
+                    }
+                }
+            }
+            if (sp == 0) break;
+            ref = stack[--sp];
+        }
+    }
+    return Hit{best, best_rec, best == LXO_NO_HIT ? INFINITY : bt};
+}
+
+__global__ void k_trace(const Scene sc, const float* __restrict__ org, const float* __restrict__ dir,
+                        const uint32_t* __restrict__ skip, const float* __restrict__ tmax, uint32_t n,
+                        uint32_t* __restrict__ hit, float* __restrict__ t, int* err)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float3 o = f3(org[3 * i], org[3 * i + 1], org[3 * i + 2]);
+    const float3 d = f3(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]);
+    Counters cnt{0, 0, 0};
+    const Hit h = closest_hit<false>(sc, o, d, skip ? skip[i] : LXO_NO_HIT, tmax ? tmax[i] : INFINITY, err, cnt);
+    hit[i] = h.id;
+    t[i] = h.t;
+}
+
+// ---------------------------------------------------------------------------
+// photon source
+// ---------------------------------------------------------------------------
+struct Photon {
+    float3 pos, dir, pol;
+    float time;
+    int medium;
+    uint32_t last;
+    uint32_t step;
+    uint64_t pid;
+};
+
+__device__ __forceinline__ float3 random_pol(float3 k, float u)
+{
+    float3 e1, e2;
+    onb(k, e1, e2);
+    float s, c;
+    sincospif(2.0f * u, &s, &c);
+    return normalize(c * e1 + s * e2);
+}
+
+__device__ __forceinline__ bool inside_poly(const SourceDev& s, float x, float y)
+{
+    if (s.n_sides <= 0) return x * x + y * y <= s.radius * s.radius;
+    for (int k = 0; k < s.n_sides; ++k)
+        if (x * s.side_cos[k] + y * s.side_sin[k] > s.apothem) return false;
+    return true;
+}
+
+__device__ Photon make_photon(const PropParams& p, uint64_t idx)
+{
+    const SourceDev& s = p.src;
+    Photon ph;
+    ph.pid = p.base + idx;
+    ph.medium = s.medium;
+    ph.time = s.t0;
+    ph.last = LXO_NO_HIT;
+    ph.step = 0;
+    if (s.kind == LXO_SRC_EXPLICIT) {
+        ph.pos = f3(s.pos[3 * idx], s.pos[3 * idx + 1], s.pos[3 * idx + 2]);
+        ph.dir = normalize(f3(s.dir[3 * idx], s.dir[3 * idx + 1], s.dir[3 * idx + 2]));
+        float3 e = f3(s.pol[3 * idx], s.pol[3 * idx + 1], s.pol[3 * idx + 2]);
+        ph.pol = normalize(e - dot(e, ph.dir) * ph.dir);
+        return ph;
+    }
+    const U4 u = draw4(p.seed, ph.pid, kSourceStep, 0);
+    const float c = 2.0f * u.u0 - 1.0f, sn = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    float sp, cp;
+    sincospif(2.0f * u.u1, &sp, &cp);
+    ph.dir = f3(sn * cp, sn * sp, c);
+    ph.pol = random_pol(ph.dir, u.u2);
+    if (s.kind == LXO_SRC_POINT) {
+        ph.pos = f3(s.center[0], s.center[1], s.center[2]);
+    } else if (s.kind == LXO_SRC_SEGMENT) {
+        ph.pos = f3(s.center[0] + u.u3 * (s.p1[0] - s.center[0]), s.center[1] + u.u3 * (s.p1[1] - s.center[1]),
+                    s.center[2] + u.u3 * (s.p1[2] - s.center[2]));
+    } else if (s.kind == LXO_SRC_BALL) {
+        ph.pos = f3(s.center[0], s.center[1], s.center[2]);
+        for (int tr = 0; tr < kMaxTries; ++tr) {
+            const U4 w = draw4(p.seed, ph.pid, kSourceStep, 1 + tr);
+            const float x = s.radius * (2.0f * w.u0 - 1.0f), y = s.radius * (2.0f * w.u1 - 1.0f),
+                        z = s.radius * (2.0f * w.u2 - 1.0f);
+            if (x * x + y * y + z * z <= s.radius * s.radius) {
+                ph.pos = f3(s.center[0] + x, s.center[1] + y, s.center[2] + z);
+                break;
+            }
+        }
+    } else {
+        ph.pos = f3(0.0f, 0.0f, s.z_min + u.u3 * (s.z_max - s.z_min));
+        for (int tr = 0; tr < kMaxTries; ++tr) {
+            const U4 w = draw4(p.seed, ph.pid, kSourceStep, 1 + tr);
+            float r = s.radius * sqrtf(w.u0), sa, ca;
+            sincospif(2.0f * w.u1, &sa, &ca);
+            if (inside_poly(s, r * ca, r * sa)) {
+                ph.pos.x = r * ca;
+                ph.pos.y = r * sa;
+                break;
+            }
+            r = s.radius * sqrtf(w.u2);
+            sincospif(2.0f * w.u3, &sa, &ca);
+            if (inside_poly(s, r * ca, r * sa)) {
+                ph.pos.x = r * ca;
+                ph.pos.y = r * sa;
+                break;
+            }
+        }
+    }
+    return ph;
+}
+
+__global__ void k_sample_source(const __grid_constant__ PropParams p, float* pos, float* dir, float* pol)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    const Photon ph = make_photon(p, i);
+    pos[3 * i] = ph.pos.x; pos[3 * i + 1] = ph.pos.y; pos[3 * i + 2] = ph.pos.z;
+    dir[3 * i] = ph.dir.x; dir[3 * i + 1] = ph.dir.y; dir[3 * i + 2] = ph.dir.z;
+    pol[3 * i] = ph.pol.x; pol[3 * i + 1] = ph.pol.y; pol[3 * i + 2] = ph.pol.z;
+}
+
+// ---------------------------------------------------------------------------
+// interactions (Sec. 2.2; Appendix items 1 and 3)
+// ---------------------------------------------------------------------------
+
+// Rayleigh scattering, dipole law: density of the new direction k' is
+// proportional to 1 - (k'.eps)^2; new polarisation = eps projected
+// perpendicular to k'.  Rejection from the isotropic distribution.
+__device__ __forceinline__ void rayleigh(Photon& ph, uint64_t seed)
+{
+    for (int tr = 0; tr < kMaxTries; ++tr) {
+        const U4 u = draw4(seed, ph.pid, ph.step, 1 + tr);
+        const float c = 2.0f * u.u0 - 1.0f, sn = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+        float sp, cp;
+        sincospif(2.0f * u.u1, &sp, &cp);
+        const float3 k = f3(sn * cp, sn * sp, c);
+        const float ce = dot(k, ph.pol);
+        if (!(u.u2 < 1.0f - ce * ce)) continue;
+        const float3 e = ph.pol - ce * k;
+        const float l2 = dot(e, e);
+        if (l2 < 1e-12f) continue;
+        ph.dir = k;
+        ph.pol = rsqrtf(l2) * e;
+        return;
+    }
+}
+
+// Lambertian reflection about the incident-side normal N (draw 1 of the step)
+__device__ __forceinline__ void lambert(Photon& ph, float3 N, uint64_t seed)
+{
+    const U4 u = draw4(seed, ph.pid, ph.step, 1);
+    const float c = sqrtf(u.u0), sn = sqrtf(fmaxf(0.0f, 1.0f - u.u0));
+    float sp, cp;
+    sincospif(2.0f * u.u1, &sp, &cp);
+    float3 t1, t2;
+    onb(N, t1, t2);
+    ph.dir = normalize(c * N + sn * (cp * t1 + sp * t2));
+    ph.pol = random_pol(ph.dir, u.u2);
+}
+
+__device__ __forceinline__ void mirror(Photon& ph, float3 N)
+{
+    const float ci = -dot(ph.dir, N);
+    const float pe = dot(ph.pol, N);
+    ph.dir = normalize(ph.dir + (2.0f * ci) * N);
+    float3 e = (2.0f * pe) * N - ph.pol;
+    e = e - dot(e, ph.dir) * ph.dir;
+    ph.pol = normalize(e);
+}
+
+// Fresnel at a bare dielectric boundary n1 -> n2 with a linearly polarised
+// photon: P(reflect) = cs^2 Rs + cp^2 Rp; outgoing polarisation is the
+// coherent sum of the s and p amplitudes (p basis = s x k of each wave;
+// magnitudes only under total internal reflection).  Normal incidence:
+// s = eps (Appendix item 1).  Returns true if reflected.
+__device__ __forceinline__ bool dielectric(Photon& ph, float3 N, float n1, float n2, float u)
+{
+    const float3 k = ph.dir;
+    const float ci = fminf(1.0f, -dot(k, N));
+    float3 s = cross(k, N);
+    const float sl2 = dot(s, s);
+    s = (sl2 < 1e-12f) ? ph.pol : rsqrtf(sl2) * s;
+    const float3 pin = cross(s, k);
+    const float cs = dot(ph.pol, s), cpv = dot(ph.pol, pin);
+    const float eta = n1 / n2;
+    const float st2 = eta * eta * (1.0f - ci * ci);
+    float rs = 1.0f, rp = 1.0f, ts = 0.0f, tp = 0.0f, ct = 0.0f, pr = 1.0f;
+    const bool tir = st2 >= 1.0f;
+    if (!tir) {
+        ct = sqrtf(1.0f - st2);
+        const float a = n1 * ci, b = n2 * ct, c2 = n2 * ci, d2 = n1 * ct;
+        rs = (a - b) / (a + b);
+        rp = (c2 - d2) / (c2 + d2);
+        ts = 2.0f * a / (a + b);
+        tp = 2.0f * a / (c2 + d2);
+        pr = cs * cs * rs * rs + cpv * cpv * rp * rp;
+    }
+    if (u < pr) {
+        const float3 kr = normalize(k + (2.0f * ci) * N);
+        const float3 pr_v = cross(s, kr);
+        const float as = tir ? cs : cs * rs, ap = tir ? cpv : cpv * rp;
+        ph.dir = kr;
+        ph.pol = normalize(as * s + ap * pr_v);
+        return true;
+    }
+    const float3 kt = normalize(eta * k + (eta * ci - ct) * N);
+    const float3 pt_v = cross(s, kt);
+    ph.dir = kt;
+    ph.pol = normalize((cs * ts) * s + (cpv * tp) * pt_v);
+    return false;
+}
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) { return fmaxf(a, fmaxf(b, c)); }
+
+// move off the surface just hit by a margin above the rounding of the hit point
+__device__ __forceinline__ void spawn_offset(Photon& ph, float3 o_ray, float t_hit, float3 N, float side)
+{
+    float m = fmaxf(fmaxf(1.0f, t_hit), fmaxf(fmax3(fabsf(ph.pos.x), fabsf(ph.pos.y), fabsf(ph.pos.z)),
+                                              fmax3(fabsf(o_ray.x), fabsf(o_ray.y), fabsf(o_ray.z))));
+    const float eps = m * 3.814697265625e-06f;  // 2^-18
+    ph.pos = ph.pos + (side * eps) * N;
+}
+
+// one interaction; returns -1 if the photon lives on, else its fate code
+// (detail set to channel / material / surface / triangle)
+template <bool kStats>
+__device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counters& cnt)
+{
+    const U4 u = draw4(p.seed, ph.pid, ph.step, 0);
+    const DevMaterial& mt = p.mat[ph.medium];
+    const float d_abs = isinf(mt.abs_len) ? INFINITY : -mt.abs_len * logf(u.u0);
+    const float d_ray = isinf(mt.ray_len) ? INFINITY : -mt.ray_len * logf(u.u1);
+    const float d_int = fminf(d_abs, d_ray);
+    const Hit h = closest_hit<kStats>(p.sc, ph.pos, ph.dir, ph.last, d_int, p.err, cnt);
+    if (h.id == LXO_NO_HIT) {
+        if (isinf(d_int)) {
+            detail = -1;
+            return LXO_FATE_ESCAPED;
+        }
+        ph.pos = ph.pos + d_int * ph.dir;
+        ph.time += d_int * mt.n_over_c;
+        if (d_abs <= d_ray) {
+            detail = ph.medium;
+            return LXO_FATE_BULK_ABS;
+        }
+        rayleigh(ph, p.seed);
+        ph.last = LXO_NO_HIT;
+        return -1;
+    }
+    const float3 o_ray = ph.pos;
+    ph.pos = ph.pos + h.t * ph.dir;
+    ph.time += h.t * mt.n_over_c;
+    // geometric normal and attributes of the triangle hit (record in leaf order)
+    const float4* tr = p.sc.tris + 3 * (size_t)h.rec;
+    const float4 va = __ldg(tr + 0), vb = __ldg(tr + 1), vc = __ldg(tr + 2);
+    const uint2 at = make_uint2(__float_as_uint(vc.z), __float_as_uint(vc.w));
+    const float3 e1 = f3(va.w - va.x, vb.x - va.y, vb.y - va.z);
+    const float3 e2 = f3(vb.z - va.x, vb.w - va.y, vc.x - va.z);
+    const float3 ng = normalize(cross(e1, e2));
+    const bool forward = dot(ph.dir, ng) > 0.0f;
+    const int mi = at.x & 0xFF, mo = (at.x >> 8) & 0xFF;
+    const uint32_t sid = at.x >> 16;
+    const int from = forward ? mi : mo, to = forward ? mo : mi;
+    const float3 Nf = forward ? (-1.0f) * ng : ng;
+    ph.last = h.id;
+    if (sid == LXO_SURF_NONE) {
+        if (from != ph.medium || to >= p.n_mat) {
+            detail = (int)h.id;
+            return LXO_FATE_GEOM_ERR;
+        }
+        const bool refl = dielectric(ph, Nf, p.mat[from].n, p.mat[to].n, u.u2);
+        if (!refl) ph.medium = to;
+        spawn_offset(ph, o_ray, h.t, Nf, refl ? 1.0f : -1.0f);
+        return -1;
+    }
+    const DevSurface& sf = p.surf[sid];
+    if (sf.type == LXO_SURF_ABSORBER) {
+        detail = (int)sid;
+        return LXO_FATE_SURF_ABS;
+    }
+    if (sf.type == LXO_SURF_PHOTOCATHODE) {
+        const int ch = (int)at.y;
+        if (ch < 0 || ch >= p.n_chan) {
+            atomicOr(p.err, kErrChannel);
+            detail = (int)h.id;
+            return LXO_FATE_GEOM_ERR;
+        }
+        detail = ch;
+        return (u.u2 < sf.qe) ? LXO_FATE_DETECTED : LXO_FATE_QE_FAIL;
+    }
+    bool specular;
+    if (sf.type == LXO_SURF_REFLECTOR) {
+        if (!(u.u2 < sf.R)) {
+            detail = (int)sid;
+            return LXO_FATE_SURF_ABS;
+        }
+        specular = u.u3 < sf.spec;
+    } else if (sf.type == LXO_SURF_ELECTRODE_T) {
+        if (u.u2 < sf.T) {
+            if (from != ph.medium || to >= p.n_mat) {
+                detail = (int)h.id;
+                return LXO_FATE_GEOM_ERR;
+            }
+            ph.medium = to;
+            spawn_offset(ph, o_ray, h.t, Nf, -1.0f);
+            return -1;
+        }
+        if (!(u.u3 < sf.Rw)) {
+            detail = (int)sid;
+            return LXO_FATE_SURF_ABS;
+        }
+        specular = draw4(p.seed, ph.pid, ph.step, 1).u3 < sf.wspec;
+    } else {
+        detail = (int)h.id;
+        return LXO_FATE_GEOM_ERR;
+    }
+    if (specular)
+        mirror(ph, Nf);
+    else
+        lambert(ph, Nf, p.seed);
+    spawn_offset(ph, o_ray, h.t, Nf, 1.0f);
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// persistent propagation kernel
+// ---------------------------------------------------------------------------
+constexpr int kPropThreads = 256;
+constexpr uint32_t kChunk = 64;
+
+template <bool kStats>
+__global__ void __launch_bounds__(kPropThreads) k_propagate(const __grid_constant__ PropParams p)
+{
+    Counters cnt{0, 0, 0};
+    uint32_t my_steps = 0;
+    __shared__ unsigned long long s_f[kMaxFates];
+    for (int i = threadIdx.x; i < p.n_fates; i += blockDim.x) s_f[i] = 0ull;
+    __syncthreads();
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    unsigned long long chunk_next = 0, chunk_end = 0;  // warp-uniform
+    bool exhausted = false;                             // warp-uniform
+    bool alive = false;
+    Photon ph;
+    const int M = p.n_mat;
+
+    while (true) {
+        uint32_t need = __ballot_sync(FULL_MASK, !alive);
+        while (need && !exhausted) {
+            if (chunk_next >= chunk_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)kChunk);
+                base = __shfl_sync(FULL_MASK, base, 0);
+                if (base >= p.n) {
+                    exhausted = true;
+                    break;
+                }
+                chunk_next = base;
+                chunk_end = min(base + kChunk, (unsigned long long)p.n);
+            }
+            const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
+            const uint32_t nneed = __popc(need);
+            const uint32_t take = min(avail, nneed);
+            const bool mine = ((need >> lane) & 1u) && (__popc(need & lt_mask) < take);
+            if (mine) {
+                ph = make_photon(p, chunk_next + __popc(need & lt_mask));
+                alive = true;
+            }
+            chunk_next += take;
+            need = __ballot_sync(FULL_MASK, !alive);
+        }
+        if (!__any_sync(FULL_MASK, alive)) break;
+        if (alive) {
+            int detail = -1;
+            int fate = photon_step<kStats>(p, ph, detail, cnt);
+            ph.step++;
+            if (kStats) my_steps++;
+            if (fate < 0 && ph.step >= p.max_steps) fate = LXO_FATE_TRUNCATED;
+            if (fate >= 0) {
+                alive = false;
+                atomicAdd(&s_f[fate], 1ull);
+                atomicAdd(&s_f[7], (unsigned long long)ph.step);
+                if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
+                if (fate == LXO_FATE_SURF_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + M + detail], 1ull);
+                if (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) {
+                    atomicAdd(&p.out.lce[detail], 1u);
+                    if (fate == LXO_FATE_DETECTED) {
+                        atomicAdd(&p.out.det[detail], 1u);
+                        const float b = floorf(ph.time / p.tbin);
+                        const uint32_t bin = (b >= (float)p.n_tbins || !(b >= 0.0f)) ? p.n_tbins : (uint32_t)b;
+                        atomicAdd(&p.out.hist[(size_t)detail * (p.n_tbins + 1) + bin], 1u);
+                    }
+                }
+                const uint64_t idx = ph.pid - p.base;
+                if (p.out.ph_fate) p.out.ph_fate[idx] = (uint32_t)fate;
+                if (p.out.ph_detail) p.out.ph_detail[idx] = detail;
+                if (p.out.ph_steps) p.out.ph_steps[idx] = ph.step;
+                if (p.out.ph_time) p.out.ph_time[idx] = ph.time;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.n_fates; i += blockDim.x)
+        if (s_f[i]) atomicAdd(&p.out.fates[i], s_f[i]);
+    if (kStats) {
+        atomicAdd(&p.out.stats[0], (unsigned long long)my_steps);
+        atomicAdd(&p.out.stats[1], (unsigned long long)cnt.nodes);
+        atomicAdd(&p.out.stats[2], (unsigned long long)cnt.leaves);
+        atomicAdd(&p.out.stats[3], (unsigned long long)cnt.tris);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_trace(const Scene& sc, const float* org, const float* dir, const uint32_t* skip,
+                         const float* tmax, uint32_t n, uint32_t* hit, float* t, int* err, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const int threads = 128;
+    k_trace<<<(n + threads - 1) / threads, threads, 0, st>>>(sc, org, dir, skip, tmax, n, hit, t, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, cudaStream_t st)
+{
+    if (p.n == 0) return cudaSuccess;
+    const int threads = 128;
+    const uint64_t blocks = (p.n + threads - 1) / threads;
+    k_sample_source<<<(unsigned)blocks, threads, 0, st>>>(p, pos, dir, pol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
+{
+    if (p.n == 0) return cudaSuccess;
+    int sms = 0, per_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    const bool stats = (p.flags & LXO_FLAG_STATS) != 0;
+    e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<true>, kPropThreads, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<false>, kPropThreads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    const uint64_t need = (p.n + kPropThreads - 1) / kPropThreads;
+    if (need < blocks) blocks = need;
+    if (stats)
+        k_propagate<true><<<(unsigned)blocks, kPropThreads, 0, st>>>(p);
+    else
+        k_propagate<false><<<(unsigned)blocks, kPropThreads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace lxo

@@ -1,0 +1,205 @@
+"""Python front end of the photon tracker (the paper's user-level flow, Sec. 1
+and 2.1: import the detector as a mesh, assign materials and surfaces,
+generate photons, propagate on the GPU, read back per-PMT hits, arrival
+times and loss bookkeeping).
+
+Everything here is argument marshalling around the C ABI in
+``include/lxo.h``; every step of the photon path runs in the CUDA library.
+PyTorch provides device memory and streams.  There is no CPU fallback: the
+constructor raises if CUDA or the library is unavailable."""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _capi as A
+from .geometry import Detector, Source, SRC_EXPLICIT
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_source(src: Source, explicit=None) -> A.lxo_source:
+    s = A.lxo_source()
+    s.kind, s.medium, s.n_sides = int(src.kind), int(src.medium), int(src.n_sides)
+    s.radius, s.phase, s.z_min, s.z_max = float(src.radius), float(src.phase), float(src.z_min), float(src.z_max)
+    s.center[:] = [float(x) for x in src.center]
+    s.p1[:] = [float(x) for x in src.p1]
+    s.t0 = float(src.t0)
+    if explicit is not None:
+        pos, dir, pol = explicit
+        s.pos, s.dir, s.pol = pos.data_ptr(), dir.data_ptr(), pol.data_ptr()
+    return s
+
+
+class Tracker:
+    """A detector loaded on one GPU with its BVH built."""
+
+    def __init__(self, det: Detector, device: int = 0, leaf_size: int = 0, sah_bins: int = 0, n_threads: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the photon tracker needs a CUDA GPU; no CPU fallback exists")
+        L = A.lib()
+        self.det = det
+        self.device = torch.device("cuda", device)
+        ctx = C.c_void_p()
+        rc = L.lxo_create(C.byref(ctx), device)
+        if rc != A.LXO_OK:
+            raise A.LxoError(rc, "lxo_create failed")
+        self._ctx = ctx
+        self._L = L
+        v = np.ascontiguousarray(det.verts, np.float32)
+        t = np.ascontiguousarray(det.tris, np.uint32)
+        mi = np.ascontiguousarray(det.mat_inner, np.uint8)
+        mo = np.ascontiguousarray(det.mat_outer, np.uint8)
+        sf = np.ascontiguousarray(det.surface, np.uint16)
+        ch = np.ascontiguousarray(det.channel, np.int32)
+        self._check(L.lxo_load_mesh(ctx, v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0], mi.ctypes.data,
+                                    mo.ctypes.data, sf.ctypes.data, ch.ctypes.data))
+        self.set_materials(det.materials)
+        self.set_surfaces(det.surfaces)
+        P = max(1, det.n_pmts)
+        pm = (A.lxo_pmt * P)()
+        for i in range(P):
+            pm[i].channel = i
+            if i < det.n_pmts:
+                pm[i].array = int(det.pmt_array[i])
+                pm[i].center[:] = [float(x) for x in det.pmt_pos[i]]
+        self._check(L.lxo_set_pmts(ctx, pm, P))
+        self.n_channels = P
+        bp = A.lxo_bvh_params(leaf_size, sah_bins, n_threads, 0)
+        info = A.lxo_bvh_info()
+        self._check(L.lxo_build_bvh(ctx, C.byref(bp), C.byref(info)))
+        self.bvh_info = {f: getattr(info, f) for f, _ in A.lxo_bvh_info._fields_}
+
+    def _check(self, rc):
+        if rc != A.LXO_OK:
+            raise A.LxoError(rc, self._L.lxo_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.lxo_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- tables -------------------------------------------------------------
+    def set_materials(self, mats):
+        arr = (A.lxo_material * len(mats))()
+        for i, m in enumerate(mats):
+            arr[i].n = m.n
+            arr[i].abs_len_mm = m.abs_len_mm if math.isfinite(m.abs_len_mm) else float("inf")
+            arr[i].rayleigh_len_mm = m.rayleigh_len_mm if math.isfinite(m.rayleigh_len_mm) else float("inf")
+        self._check(self._L.lxo_set_materials(self._ctx, arr, len(mats)))
+        self.n_materials = len(mats)
+
+    def set_surfaces(self, surfs):
+        arr = (A.lxo_surface * max(1, len(surfs)))()
+        for i, s in enumerate(surfs):
+            arr[i].type, arr[i].reflectivity, arr[i].spec_frac, arr[i].qe = s.type, s.reflectivity, s.spec_frac, s.qe
+            arr[i].transparency, arr[i].wire_reflectivity = s.transparency, s.wire_reflectivity
+            arr[i].wire_spec_frac = s.wire_spec_frac
+        self._check(self._L.lxo_set_surfaces(self._ctx, arr, len(surfs)))
+        self.n_surfaces = len(surfs)
+
+    @property
+    def n_fates(self):
+        return A.LXO_FATES_FIXED + self.n_materials + self.n_surfaces
+
+    # -- geometry query -----------------------------------------------------
+    def trace_rays(self, org, dir, skip=None, tmax=None, stream=None):
+        org = org.contiguous()
+        dir = dir.contiguous()
+        n = org.shape[0]
+        hit = torch.empty(n, dtype=torch.int32, device=self.device)
+        t = torch.empty(n, dtype=torch.float32, device=self.device)
+        sk = None if skip is None else skip.to(torch.int32).contiguous()
+        tm = None if tmax is None else tmax.contiguous()
+        self._check(self._L.lxo_trace_rays(self._ctx, _ptr(org), _ptr(dir), _ptr(sk), _ptr(tm), n, _ptr(hit),
+                                           _ptr(t), _stream(stream)))
+        return hit, t
+
+    def sample_source(self, n, base=0, seed=0, source=None, stream=None):
+        src = make_source(source or self.det.source)
+        pos = torch.empty((n, 3), dtype=torch.float32, device=self.device)
+        dir = torch.empty_like(pos)
+        pol = torch.empty_like(pos)
+        self._check(self._L.lxo_sample_source(self._ctx, C.byref(src), n, base, seed, _ptr(pos), _ptr(dir), _ptr(pol),
+                                              _stream(stream)))
+        return pos, dir, pol
+
+    # -- propagation --------------------------------------------------------
+    def alloc_results(self, n_tbins=1000, per_photon_n=0):
+        P, dev = self.n_channels, self.device
+        out = dict(lce=torch.zeros(P, dtype=torch.int32, device=dev),
+                   det=torch.zeros(P, dtype=torch.int32, device=dev),
+                   hist=torch.zeros((P, n_tbins + 1), dtype=torch.int32, device=dev),
+                   fates=torch.zeros(self.n_fates, dtype=torch.int64, device=dev))
+        if per_photon_n:
+            out.update(fate=torch.zeros(per_photon_n, dtype=torch.int32, device=dev),
+                       detail=torch.zeros(per_photon_n, dtype=torch.int32, device=dev),
+                       steps=torch.zeros(per_photon_n, dtype=torch.int32, device=dev),
+                       time=torch.zeros(per_photon_n, dtype=torch.float32, device=dev))
+        return out
+
+    def _results(self, out):
+        r = A.lxo_results()
+        r.lce, r.det, r.hist, r.fates = (out[k].data_ptr() for k in ("lce", "det", "hist", "fates"))
+        if "fate" in out:
+            r.ph_fate, r.ph_detail = out["fate"].data_ptr(), out["detail"].data_ptr()
+            r.ph_steps, r.ph_time = out["steps"].data_ptr(), out["time"].data_ptr()
+        if "stats" in out:
+            r.stats = out["stats"].data_ptr()
+        return r
+
+    def propagate(self, n, base=0, seed=0, source=None, explicit=None, max_steps=10000, n_tbins=1000, tbin_ns=1.0,
+                  per_photon=False, out=None, stream=None, sync=True, stats=False):
+        """Propagates photons base..base+n-1; returns (accumulates into) a dict
+        of device tensors: lce, det [P], hist [P, n_tbins+1], fates [8+M+S]
+        and, with per_photon, fate / detail / steps / time [n]; with stats,
+        stats [4] = steps, nodes visited, leaves visited, triangles tested."""
+        if out is None:
+            out = self.alloc_results(n_tbins, n if per_photon else 0)
+        if stats and "stats" not in out:
+            out["stats"] = torch.zeros(4, dtype=torch.int64, device=self.device)
+        src = make_source(source or self.det.source, explicit)
+        if explicit is not None and src.kind != SRC_EXPLICIT:
+            raise ValueError("explicit arrays need an SRC_EXPLICIT source")
+        rp = A.lxo_run_params(seed, max_steps, n_tbins, tbin_ns, A.LXO_FLAG_STATS if stats else 0)
+        res = self._results(out)
+        st = _stream(stream)
+        self._check(self._L.lxo_propagate(self._ctx, C.byref(src), n, base, C.byref(rp), C.byref(res), st))
+        if sync:
+            self._check(self._L.lxo_sync(self._ctx, st))
+        return out
+
+    def propagate_host(self, n, base=0, seed=0, source=None, max_steps=10000, n_tbins=1000, tbin_ns=1.0,
+                       out=None, stream=None):
+        """End-to-end call with host (numpy) result buffers."""
+        P = self.n_channels
+        if out is None:
+            out = dict(lce=np.zeros(P, np.uint32), det=np.zeros(P, np.uint32),
+                       hist=np.zeros((P, n_tbins + 1), np.uint32), fates=np.zeros(self.n_fates, np.uint64))
+        src = make_source(source or self.det.source)
+        rp = A.lxo_run_params(seed, max_steps, n_tbins, tbin_ns, 0)
+        r = A.lxo_results()
+        r.lce, r.det, r.hist, r.fates = (out[k].ctypes.data for k in ("lce", "det", "hist", "fates"))
+        self._check(self._L.lxo_propagate_host(self._ctx, C.byref(src), n, base, C.byref(rp), C.byref(r),
+                                               _stream(stream)))
+        return out
+
+    def sync(self, stream=None):
+        self._check(self._L.lxo_sync(self._ctx, _stream(stream)))

@@ -1,0 +1,41 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/lxo.h; the binding uses the same names."""
+import ctypes
+import os
+import re
+
+from paper_2203_14354_gb300 import _capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(lxo_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert {"lxo_create", "lxo_propagate", "lxo_trace_rays", "lxo_build_bvh"} <= names
+    lib = ctypes.CDLL(_capi.lib_path() if os.path.exists(_capi.lib_path()) else _capi.lib()._name)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    assert declared_symbols() == set(_capi._SIGNATURES)
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        return
+    L = _capi.lib()
+    ctx = ctypes.c_void_p()
+    assert L.lxo_create(ctypes.byref(ctx), 0) != 0
+    assert not ctx.value
