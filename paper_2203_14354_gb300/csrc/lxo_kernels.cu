@@ -78,7 +78,7 @@ __device__ __forceinline__ float3 normalize(float3 a) { return rsqrtf(dot(a, a))
 // orthonormal basis perpendicular to unit n (Duff et al., JCGT 6(1), 2017)
 __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2)
 {
-    float sgn = copysignf(1.0f, n.z);
+    const float sgn = (n.z >= 0.0f) ? 1.0f : -1.0f;  // -0.0 counts as positive
     float a = -1.0f / (sgn + n.z);
     float b = n.x * n.y * a;
     t1 = f3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);

@@ -105,8 +105,10 @@ def test_trace_single_triangle_and_empty_batch(Tracker):
                      np.full(1, g.SURF_NONE, np.uint16), np.full(1, -1, np.int32), [g.Material("m", 1.0)], [],
                      np.zeros(0, np.int32), np.zeros((0, 3), np.float32), g.Source(g.SRC_POINT))
     trk = Tracker(det)
-    h, t = gpu_trace(trk, np.array([[0.2, 0.2, 0.0], [2, 2, 0]]), np.array([[0, 0, 1.0], [0, 0, 1.0]]))
-    assert list(h) == [0, NO] and t[0] == 5.0
+    org, d = np.array([[0.2, 0.2, 0.0], [2, 2, 0]], np.float32), np.array([[0, 0, 1.0], [0, 0, 1.0]], np.float32)
+    h, t = gpu_trace(trk, org, d)
+    assert list(h) == [0, NO] and t[0] == pytest.approx(5.0, rel=1e-6)
+    assert_same(h, t, *O.Oracle(det).trace(org, d, brute=True))
     h, t = gpu_trace(trk, np.zeros((0, 3)), np.zeros((0, 3)))
     assert h.size == 0
 
