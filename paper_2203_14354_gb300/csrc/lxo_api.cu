@@ -155,6 +155,7 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
     if (src->kind == LXO_SRC_VOLUME_POLYGON && src->n_sides > 0) {
         const double pi = 3.141592653589793;
         sd.apothem = (float)((double)src->radius * cos(pi / src->n_sides));
+        sd.phase_turns = (float)((double)src->phase / (2.0 * pi));
         for (int k = 0; k < src->n_sides; ++k) {
             const double a = (double)src->phase + 2.0 * pi * (k + 0.5) / src->n_sides;
             sd.side_cos[k] = (float)cos(a);

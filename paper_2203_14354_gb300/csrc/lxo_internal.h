@@ -64,6 +64,7 @@ struct Scene {
 struct SourceDev {
     int kind, medium, n_sides;
     float radius, z_min, z_max, apothem, t0;
+    float phase_turns;    // polygon phase / (2 pi)
     float center[3], p1[3];
     float side_cos[kMaxPolySides], side_sin[kMaxPolySides];
     const float* pos;

@@ -176,6 +176,40 @@ struct Counters {
     uint32_t nodes, leaves, tris;
 };
 
+// Leaf test of one leaf reference: every triangle of the leaf through the
+// exact watertight test, keeping (t, id) minimal in that order.
+template <bool kStats>
+__device__ __forceinline__ void test_leaf(const Scene& sc, const WRay& wr, int ref, uint32_t skip, float& bt,
+                                          uint32_t& best, uint32_t& best_rec, Counters& cnt)
+{
+    const uint32_t enc = ~(uint32_t)ref;
+    const uint32_t first = enc >> 3, count = (enc & 7u) + 1u;
+    if (kStats) {
+        cnt.leaves++;
+        cnt.tris += count;
+    }
+    for (uint32_t k = 0; k < count; ++k) {
+        const float4* tr = sc.tris + 3 * (size_t)(first + k);
+        const float4 a = __ldg(tr + 0), b = __ldg(tr + 1), c = __ldg(tr + 2);
+        const uint32_t id = __float_as_uint(c.y);
+        if (id == skip) continue;
+        float t;
+        if (wray_hit(wr, a, b, c, bt, t)) {
+            if (t < bt || (t == bt && (best == LXO_NO_HIT || id < best))) {
+                bt = t;
+                best = id;
+                best_rec = first + k;
+            }
+        }
+    }
+}
+
+constexpr int kDone = INT32_MIN + 1;  // stack sentinel; never a valid leaf reference (< 2^28 records)
+
+// "while-while" traversal with postponed leaves (Aila & Laine, HPG 2009): a
+// lane that reaches a leaf parks it and keeps descending until every active
+// lane of the warp holds a leaf; then the warp tests leaves together.  This
+// keeps the node loop and the triangle loop from interleaving divergently.
 template <bool kStats>
 __device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, float tmax, int* err, Counters& cnt)
 {
@@ -185,12 +219,14 @@ __device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, f
     uint32_t best = LXO_NO_HIT, best_rec = 0;
     float bt = tmax;
     int stack[kStackSize];
-    int sp = 0;
-    int ref = 0;
-    while (true) {
-        if (ref >= 0) {
+    stack[0] = kDone;
+    int sp = 1;
+    int node = 0;   // root
+    int leaf = 0;   // parked leaf (0 = none: reference 0 is the root, never a leaf)
+    while (node != kDone) {
+        while (node >= 0) {
             if (kStats) cnt.nodes++;
-            const float4* nd = sc.nodes + 4 * (size_t)ref;
+            const float4* nd = sc.nodes + 4 * (size_t)node;
             const float4 nx = __ldg(nd + 0), ny = __ldg(nd + 1), nz = __ldg(nd + 2);
             const int4 cr = __ldg(reinterpret_cast<const int4*>(nd + 3));
             const float lim = bt * kBoxSlack;
@@ -206,47 +242,34 @@ __device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, f
             const float bf = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), lim));
             const bool ha = an <= af;
             const bool hb = (bn <= bf) && (cr.y != kEmptyChild);
-            if (ha && hb) {
-                const bool a_first = an <= bn;
-                const int nearr = a_first ? cr.x : cr.y;
-                const int farr = a_first ? cr.y : cr.x;
-                if (sp >= kStackSize) {
-                    atomicOr(err, kErrStack);
-                    break;
-                }
-                stack[sp++] = farr;
-                ref = nearr;
-            } else if (ha) {
-                ref = cr.x;
-            } else if (hb) {
-                ref = cr.y;
+            if (!ha && !hb) {
+                node = stack[--sp];
             } else {
-                if (sp == 0) break;
-                ref = stack[--sp];
-            }
-        } else {
-            const uint32_t enc = ~(uint32_t)ref;
-            const uint32_t first = enc >> 3, count = (enc & 7u) + 1u;
-            if (kStats) {
-                cnt.leaves++;
-                cnt.tris += count;
-            }
-            for (uint32_t k = 0; k < count; ++k) {
-                const float4* tr = sc.tris + 3 * (size_t)(first + k);
-                const float4 a = __ldg(tr + 0), b = __ldg(tr + 1), c = __ldg(tr + 2);
-                const uint32_t id = __float_as_uint(c.y);
-                if (id == skip) continue;
-                float t;
-                if (wray_hit(wr, a, b, c, bt, t)) {
-                    if (t < bt || (t == bt && (best == LXO_NO_HIT || id < best))) {
-                        bt = t;
-                        best = id;
-                        best_rec = first + k;
+                const bool a_first = ha && (!hb || an <= bn);
+                node = a_first ? cr.x : cr.y;
+                if (ha && hb) {
+                    if (sp >= kStackSize) {
+                        atomicOr(err, kErrStack);
+                        node = kDone;
+                        sp = 1;
+                        break;
                     }
+                    stack[sp++] = a_first ? cr.y : cr.x;
                 }
             }
-            if (sp == 0) break;
-            ref = stack[--sp];
+            if (node < 0 && node != kDone && leaf == 0) {
+                leaf = node;
+                node = stack[--sp];
+            }
+            if (!__any_sync(__activemask(), leaf == 0)) break;
+        }
+        while (leaf != 0) {
+            test_leaf<kStats>(sc, wr, leaf, skip, bt, best, best_rec, cnt);
+            leaf = 0;
+            if (node < 0 && node != kDone) {
+                leaf = node;
+                node = stack[--sp];
+            }
         }
     }
     return Hit{best, best_rec, best == LXO_NO_HIT ? INFINITY : bt};
@@ -287,12 +310,16 @@ __device__ __forceinline__ float3 random_pol(float3 k, float u)
     return normalize(c * e1 + s * e2);
 }
 
-__device__ __forceinline__ bool inside_poly(const SourceDev& s, float x, float y)
+// Inside the regular polygon?  The point was drawn at azimuth 2 pi u inside
+// the circumscribed circle, so only the side of its angular sector can bound
+// it (the polygon is the union of the triangles centre-side).
+__device__ __forceinline__ bool inside_poly(const SourceDev& s, float x, float y, float u_azimuth)
 {
-    if (s.n_sides <= 0) return x * x + y * y <= s.radius * s.radius;
-    for (int k = 0; k < s.n_sides; ++k)
-        if (x * s.side_cos[k] + y * s.side_sin[k] > s.apothem) return false;
-    return true;
+    if (s.n_sides <= 0) return true;
+    float t = u_azimuth - s.phase_turns;
+    t -= floorf(t);
+    const int k = min((int)(t * (float)s.n_sides), s.n_sides - 1);
+    return x * s.side_cos[k] + y * s.side_sin[k] <= s.apothem;
 }
 
 __device__ Photon make_photon(const PropParams& p, uint64_t idx)
@@ -339,14 +366,14 @@ __device__ Photon make_photon(const PropParams& p, uint64_t idx)
             const U4 w = draw4(p.seed, ph.pid, kSourceStep, 1 + tr);
             float r = s.radius * sqrtf(w.u0), sa, ca;
             sincospif(2.0f * w.u1, &sa, &ca);
-            if (inside_poly(s, r * ca, r * sa)) {
+            if (inside_poly(s, r * ca, r * sa, w.u1)) {
                 ph.pos.x = r * ca;
                 ph.pos.y = r * sa;
                 break;
             }
             r = s.radius * sqrtf(w.u2);
             sincospif(2.0f * w.u3, &sa, &ca);
-            if (inside_poly(s, r * ca, r * sa)) {
+            if (inside_poly(s, r * ca, r * sa, w.u3)) {
                 ph.pos.x = r * ca;
                 ph.pos.y = r * sa;
                 break;
@@ -574,9 +601,49 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
 // ---------------------------------------------------------------------------
 constexpr int kPropThreads = 256;
 constexpr uint32_t kChunk = 64;
+// tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
+// idle; 4 CTAs of 256 threads per SM (64 registers) hides more L1/L2 latency
+// than 3 CTAs at 80 registers
+#ifndef LXO_REFILL_MIN
+#define LXO_REFILL_MIN 1
+#endif
+#ifndef LXO_MIN_BLOCKS
+#define LXO_MIN_BLOCKS 4
+#endif
 
+// Tally of one photon's fate: shared-memory fate counters, global per-channel
+// counts and arrival-time histogram, optional per-photon record.
+__device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s_f, const Photon& ph, int fate,
+                                      int detail)
+{
+    atomicAdd(&s_f[fate], 1ull);
+    atomicAdd(&s_f[7], (unsigned long long)ph.step);
+    if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
+    if (fate == LXO_FATE_SURF_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + p.n_mat + detail], 1ull);
+    if (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) {
+        atomicAdd(&p.out.lce[detail], 1u);
+        if (fate == LXO_FATE_DETECTED) {
+            atomicAdd(&p.out.det[detail], 1u);
+            const float b = floorf(ph.time / p.tbin);
+            const uint32_t bin = (b >= (float)p.n_tbins || !(b >= 0.0f)) ? p.n_tbins : (uint32_t)b;
+            atomicAdd(&p.out.hist[(size_t)detail * (p.n_tbins + 1) + bin], 1u);
+        }
+    }
+    const uint64_t idx = ph.pid - p.base;
+    if (p.out.ph_fate) p.out.ph_fate[idx] = (uint32_t)fate;
+    if (p.out.ph_detail) p.out.ph_detail[idx] = detail;
+    if (p.out.ph_steps) p.out.ph_steps[idx] = ph.step;
+    if (p.out.ph_time) p.out.ph_time[idx] = ph.time;
+}
+
+// Persistent photon loop.  A lane whose photon reached its fate stays idle
+// until at least LXO_REFILL_MIN lanes of its warp are idle (or all are); then
+// the idle lanes record their tallies together and take the next photon ids
+// from a warp-local chunk (ballot + prefix popcount), chunks of kChunk ids
+// coming from the global work-queue head.  Source sampling and tallies thus
+// run on many lanes at once instead of one lane per iteration.
 template <bool kStats>
-__global__ void __launch_bounds__(kPropThreads) k_propagate(const __grid_constant__ PropParams p)
+__global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(const __grid_constant__ PropParams p)
 {
     Counters cnt{0, 0, 0};
     uint32_t my_steps = 0;
@@ -588,62 +655,50 @@ __global__ void __launch_bounds__(kPropThreads) k_propagate(const __grid_constan
     const uint32_t lt_mask = (1u << lane) - 1u;
     unsigned long long chunk_next = 0, chunk_end = 0;  // warp-uniform
     bool exhausted = false;                             // warp-uniform
-    bool alive = false;
+    bool alive = false, pending = false;
+    int fate = 0, detail = -1;
     Photon ph;
-    const int M = p.n_mat;
 
     while (true) {
         uint32_t need = __ballot_sync(FULL_MASK, !alive);
-        while (need && !exhausted) {
-            if (chunk_next >= chunk_end) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)kChunk);
-                base = __shfl_sync(FULL_MASK, base, 0);
-                if (base >= p.n) {
-                    exhausted = true;
-                    break;
+        const int idle = __popc(need);
+        if (idle >= LXO_REFILL_MIN || idle == 32) {
+            if (pending) {
+                tally(p, s_f, ph, fate, detail);
+                pending = false;
+            }
+            while (need && !exhausted) {
+                if (chunk_next >= chunk_end) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)kChunk);
+                    base = __shfl_sync(FULL_MASK, base, 0);
+                    if (base >= p.n) {
+                        exhausted = true;
+                        break;
+                    }
+                    chunk_next = base;
+                    chunk_end = min(base + kChunk, (unsigned long long)p.n);
                 }
-                chunk_next = base;
-                chunk_end = min(base + kChunk, (unsigned long long)p.n);
+                const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
+                const uint32_t take = min(avail, (uint32_t)__popc(need));
+                const uint32_t rank = __popc(need & lt_mask);
+                if (((need >> lane) & 1u) && rank < take) {
+                    ph = make_photon(p, chunk_next + rank);
+                    alive = true;
+                }
+                chunk_next += take;
+                need = __ballot_sync(FULL_MASK, !alive);
             }
-            const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
-            const uint32_t nneed = __popc(need);
-            const uint32_t take = min(avail, nneed);
-            const bool mine = ((need >> lane) & 1u) && (__popc(need & lt_mask) < take);
-            if (mine) {
-                ph = make_photon(p, chunk_next + __popc(need & lt_mask));
-                alive = true;
-            }
-            chunk_next += take;
-            need = __ballot_sync(FULL_MASK, !alive);
         }
-        if (!__any_sync(FULL_MASK, alive)) break;
+        if (!__any_sync(FULL_MASK, alive || pending)) break;
         if (alive) {
-            int detail = -1;
-            int fate = photon_step<kStats>(p, ph, detail, cnt);
+            fate = photon_step<kStats>(p, ph, detail, cnt);
             ph.step++;
             if (kStats) my_steps++;
             if (fate < 0 && ph.step >= p.max_steps) fate = LXO_FATE_TRUNCATED;
             if (fate >= 0) {
                 alive = false;
-                atomicAdd(&s_f[fate], 1ull);
-                atomicAdd(&s_f[7], (unsigned long long)ph.step);
-                if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
-                if (fate == LXO_FATE_SURF_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + M + detail], 1ull);
-                if (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) {
-                    atomicAdd(&p.out.lce[detail], 1u);
-                    if (fate == LXO_FATE_DETECTED) {
-                        atomicAdd(&p.out.det[detail], 1u);
-                        const float b = floorf(ph.time / p.tbin);
-                        const uint32_t bin = (b >= (float)p.n_tbins || !(b >= 0.0f)) ? p.n_tbins : (uint32_t)b;
-                        atomicAdd(&p.out.hist[(size_t)detail * (p.n_tbins + 1) + bin], 1u);
-                    }
-                }
-                const uint64_t idx = ph.pid - p.base;
-                if (p.out.ph_fate) p.out.ph_fate[idx] = (uint32_t)fate;
-                if (p.out.ph_detail) p.out.ph_detail[idx] = detail;
-                if (p.out.ph_steps) p.out.ph_steps[idx] = ph.step;
-                if (p.out.ph_time) p.out.ph_time[idx] = ph.time;
+                pending = true;
             }
         }
     }
