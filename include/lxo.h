@@ -239,6 +239,39 @@ lxo_status lxo_propagate_host(lxo_ctx* ctx, const lxo_source* src, uint64_t n, u
  * lxo_sync (then clears it). */
 lxo_status lxo_sync(lxo_ctx* ctx, void* stream);
 
+/* Size of the library's static device scratch used by
+ * lxo_propagate_host_static (held on every GPU that loads the library until
+ * the process exits). */
+#define LXO_STATIC_SCRATCH_BYTES (8u << 20)
+
+/* lxo_propagate_host for callers that must not allocate device memory.
+ * (This entry point has no counterpart in the paper: it is a deployment
+ * variant.)  Some callers cannot call cudaMalloc once they are running: a
+ * host framework that hands out all device memory from its own fixed pool,
+ * or a data-acquisition loop that must never block, since cudaMalloc can
+ * fail mid-run and cudaFree waits for the whole device.  lxo_propagate_host
+ * allocates its device tallies on first use; this variant keeps them, with
+ * the work-queue head and the error word, in one static device array of
+ * LXO_STATIC_SCRATCH_BYTES inside the library, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *  - Same arguments and result as lxo_propagate_host: the tallies are ADDED
+ *    to the caller's host arrays (lce, det [P], hist [P*(n_tbins+1)],
+ *    fates [8+M+S]); per-photon outputs and LXO_FLAG_STATS are rejected.
+ *  - Returns LXO_ERR_ARG if 256 + 8*(8+M+S) + 4*(2P + P*(n_tbins+1)) bytes
+ *    exceed LXO_STATIC_SCRATCH_BYTES (the DARWIN-scale detector with 1000
+ *    time bins needs 7.1 MB).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and may load the library's device code: make it
+ *    before any stream capture.
+ *  - Every call on a device shares the one array, and each call overwrites
+ *    it; calls that overlap on the GPU (other streams or threads) race and
+ *    corrupt each other's results.  Synchronous.
+ *  - On success it allocates nothing, on the device or the host; the
+ *    messages of its own argument checks are cut to the context string's
+ *    current capacity. */
+lxo_status lxo_propagate_host_static(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
+                                     const lxo_run_params* params, const lxo_results* host_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

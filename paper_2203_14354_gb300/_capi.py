@@ -16,6 +16,7 @@ LXO_MAX_SURFACES = 48
 LXO_SURF_NONE = 0xFFFF
 LXO_NO_HIT = 0xFFFFFFFF
 LXO_FLAG_STATS = 1
+LXO_STATIC_SCRATCH_BYTES = 8 << 20
 FATE_NAMES = ["detected", "qe_fail", "bulk_abs", "surf_abs", "escaped", "truncated", "geom_err"]
 
 
@@ -78,6 +79,8 @@ _SIGNATURES = {
     "lxo_propagate_host": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,
                                      C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
     "lxo_sync": (C.c_int, [vp, vp]),
+    "lxo_propagate_host_static": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,
+                                            C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
 }
 
 _lib = None

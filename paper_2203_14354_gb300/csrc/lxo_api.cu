@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -464,3 +465,95 @@ lxo_status lxo_sync(lxo_ctx* c, void* stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of lxo_propagate_host.
+//
+// Its device scratch (work-queue head, error word and the device copy of the
+// tallies) lives in the file-scope array below instead of memory obtained
+// from cudaMalloc.  The array is part of this file's device module, so every
+// GPU that loads the library holds LXO_STATIC_SCRATCH_BYTES of it until the
+// process exits.  Host code cannot use the array's name as a device address:
+// the address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[LXO_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_addr[kMaxStaticDevices] = {};
+
+// error message without growing the context's string (no host allocation)
+lxo_status static_fail(lxo_ctx* c, lxo_status code, const char* msg)
+{
+    const size_t cap = c->err.capacity();
+    const size_t len = strlen(msg);
+    c->err.assign(msg, len < cap ? len : cap);
+    return code;
+}
+
+}  // namespace
+
+extern "C" lxo_status lxo_propagate_host_static(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base,
+                                                const lxo_run_params* rp, const lxo_results* host_out, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!rp) return static_fail(c, LXO_ERR_ARG, "run params are NULL");
+    if (!host_out || !host_out->lce || !host_out->det || !host_out->hist || !host_out->fates)
+        return static_fail(c, LXO_ERR_ARG, "lce, det, hist, fates host buffers required");
+    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->stats ||
+        (rp->flags & LXO_FLAG_STATS))
+        return static_fail(c, LXO_ERR_ARG, "per-photon outputs and stats unsupported");
+    lxo_status s = validate(c);
+    if (s) return s;
+    const uint64_t P = c->pmts.size(), B = (uint64_t)rp->n_tbins + 1;
+    const uint64_t NF = LXO_FATES_FIXED + c->mats.size() + c->surfs.size();
+    // layout: [0, 8) queue head, [8, 12) error word, tallies from offset 256
+    const uint64_t fates_off = 256, lce_off = fates_off + 8 * NF, det_off = lce_off + 4 * P, hist_off = det_off + 4 * P;
+    const uint64_t need = hist_off + 4 * P * B;
+    if (B > (1ull << 32) || need > (uint64_t)LXO_STATIC_SCRATCH_BYTES)
+        return static_fail(c, LXO_ERR_ARG, "tallies exceed LXO_STATIC_SCRATCH_BYTES");
+    DeviceGuard g(c->device);
+    if (c->device < 0 || c->device >= kMaxStaticDevices) return static_fail(c, LXO_ERR_ARG, "device index");
+    unsigned char* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_addr[c->device]) {
+            void* addr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
+            if (e != cudaSuccess) return static_fail(c, LXO_ERR_CUDA, "cudaGetSymbolAddress failed");
+            g_static_addr[c->device] = (unsigned char*)addr;
+        }
+        scratch = g_static_addr[c->device];
+    }
+    lxo::PropParams p;
+    s = fill_params(c, src, n, base, rp, &p);
+    if (s) return s;
+    p.queue = (unsigned long long*)scratch;
+    p.err = (int*)(scratch + 8);
+    memset(&p.out, 0, sizeof p.out);
+    p.out.fates = (unsigned long long*)(scratch + fates_off);
+    p.out.lce = (uint32_t*)(scratch + lce_off);
+    p.out.det = (uint32_t*)(scratch + det_off);
+    p.out.hist = (uint32_t*)(scratch + hist_off);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: reset the queue head and
+    // error word, and start the tallies from the caller's values
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.out.fates, host_out->fates, 8 * NF, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.out.lce, host_out->lce, 4 * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.out.det, host_out->det, 4 * P, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.out.hist, host_out->hist, 4 * P * B, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n > 0) e = lxo::launch_propagate(p, c->device, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->fates, p.out.fates, 8 * NF, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->lce, p.out.lce, 4 * P, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->det, p.out.det, 4 * P, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->hist, p.out.hist, 4 * P * B, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return static_fail(c, LXO_ERR_CUDA, cudaGetErrorString(e));
+    if (herr) return static_fail(c, LXO_ERR_DEVICE, "device fault flags set");
+    return LXO_OK;
+}
