@@ -33,6 +33,12 @@ import numpy as np  # noqa: E402
 
 METRIC = "photons/sec to fate, DARWIN mesh, 1 GB300"
 UNIT = "photons/s"
+OPS_PER_NODE, OPS_PER_TRI, OPS_PHYSICS = 40, 50, 250
+N_SM, LANES_PER_SM = 152, 128
+# DRAM bytes (read + write) per photon of the propagation kernel, from the ncu
+# capture summarised in profiles/ (None while the kernel differs from the one
+# captured)
+DRAM_BYTES_PER_PHOTON = 2352  # profiles/k_propagate_darwin.md (2e6-photon capture, scaled per photon)
 
 
 def parse():
@@ -229,12 +235,20 @@ def main():
     st_out = trk.alloc_results(1000)
     trk.propagate(n, base=base0 + args.warmup * n, seed=1, out=st_out, stats=True)
     stats = st_out["stats"].cpu().numpy().astype(np.float64)
-    steps_total, nodes, leaves, tris = stats
+    steps_total, nodes, leaves, tris, node_it, leaf_it, outer_it, trav_cyc, loop_cyc = stats[:9]
+    simd = {"node_loop": nodes / max(32 * node_it, 1), "leaf_loop": leaves / max(32 * leaf_it, 1),
+            "photon_loop": steps_total / max(32 * outer_it, 1), "traversal_cycle_share": trav_cyc / max(loop_cyc, 1)}
     bytes_per_step = (nodes * 64 + tris * 48) / steps_total
     kern_s = statistics.mean(kern_ms) / 1e3
-    achieved = steps_total * bytes_per_step / kern_s / 1e9
+    fetch_gbs = steps_total * bytes_per_step / kern_s / 1e9
+    # algorithmic lane operations per photon step: 40 per BVH node visit (two slab
+    # tests), 50 per triangle test (watertight), 250 of physics (Philox, logs,
+    # interaction); peak = 152 SMs x 128 FP32/INT32 lanes x max SM clock
+    ops_per_step = (nodes * OPS_PER_NODE + tris * OPS_PER_TRI) / steps_total + OPS_PHYSICS
+    achieved = steps_total * ops_per_step / kern_s / 1e9
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alu_peak = N_SM * LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
 
     # end to end through the C ABI with host result buffers (copies in the timed region)
     e2e_steps = max(1, min(args.steps, 3))
@@ -265,12 +279,18 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(n, world),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "peak_source": peak_kind,
-                         "algorithmic_bytes": "per photon step: BVH nodes visited x 64 B + triangles tested x 48 B",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                         "unit": "G lane-ops/s (FP32/INT32)", "frac": achieved / alu_peak,
+                         "traffic": DRAM_BYTES_PER_PHOTON * n if DRAM_BYTES_PER_PHOTON else None,
+                         "peak_source": f"{N_SM} SMs x {LANES_PER_SM} lanes x sm_max_mhz ({peak_kind})",
+                         "algorithmic_ops": f"per photon step: {OPS_PER_NODE} per node visit + {OPS_PER_TRI} per "
+                                            f"triangle test + {OPS_PHYSICS} physics",
                          "per_step": {"nodes": nodes / steps_total, "leaves": leaves / steps_total,
-                                      "triangles": tris / steps_total, "bytes": bytes_per_step},
-                         "steps_per_photon": steps_total / n, "kernel_ms": statistics.mean(kern_ms)},
+                                      "triangles": tris / steps_total, "ops": ops_per_step,
+                                      "fetch_bytes": bytes_per_step},
+                         "fetch": {"achieved_gbs": fetch_gbs, "hbm_peak_gbs": hbm, "frac_of_hbm": fetch_gbs / hbm},
+                         "steps_per_photon": steps_total / n, "kernel_ms": statistics.mean(kern_ms),
+                         "simd_efficiency": simd},
             "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * 1,

@@ -164,8 +164,13 @@ typedef struct {
     int32_t* ph_detail;          /* optional device [n]: channel / material / surface / triangle */
     uint32_t* ph_steps;          /* optional device [n] */
     float* ph_time;              /* optional device [n]: time at the end, ns */
-    unsigned long long* stats;   /* device [4] with LXO_FLAG_STATS: steps, BVH nodes visited,
-                                    leaves visited, triangles tested (accumulated) */
+    unsigned long long* stats;   /* device [32] with LXO_FLAG_STATS (accumulated): [0..3] photon steps,
+                                    BVH nodes visited, leaves visited, triangles tested (lane counts);
+                                    [4..6] warp iterations of the node loop, of the leaf loop and of
+                                    the photon loop; [7..8] lane cycles in traversal, in steps;
+                                    [9..17] steps in material 0 by nodes visited (bins of 8, last
+                                    >= 64), [18] their leaves; [19..28] the same for other
+                                    materials */
 } lxo_results;
 
 typedef struct {

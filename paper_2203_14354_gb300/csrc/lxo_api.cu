@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -31,6 +32,8 @@ struct lxo_ctx {
     // device
     float4* d_nodes = nullptr;
     float4* d_tris = nullptr;
+    int32_t* d_cells = nullptr;
+    lxo::Scene scene{};
     unsigned long long* d_queue = nullptr;  // scratch: work-queue head
     int* d_err = nullptr;                   // scratch: device error word
     void* d_tally = nullptr;                // tallies of lxo_propagate_host
@@ -77,8 +80,11 @@ void free_device_geometry(lxo_ctx* c)
 {
     if (c->d_nodes) cudaFree(c->d_nodes);
     if (c->d_tris) cudaFree(c->d_tris);
+    if (c->d_cells) cudaFree(c->d_cells);
     c->d_nodes = nullptr;
     c->d_tris = nullptr;
+    c->d_cells = nullptr;
+    c->scene = lxo::Scene{};
     c->have_bvh = false;
 }
 
@@ -111,9 +117,7 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
     if (!src) return fail(c, LXO_ERR_ARG, "source is NULL");
     memset(p, 0, sizeof *p);
     const int M = (int)c->mats.size(), S = (int)c->surfs.size();
-    p->sc.nodes = c->d_nodes;
-    p->sc.tris = c->d_tris;
-    p->sc.n_tris = c->nt;
+    p->sc = c->scene;
     for (int m = 0; m < M; ++m) {
         const lxo_material& x = c->mats[m];
         p->mat[m].n = x.n;
@@ -311,7 +315,12 @@ lxo_status lxo_build_bvh(lxo_ctx* c, const lxo_bvh_params* bp, lxo_bvh_info* inf
     char msg[256] = {0};
     // widen boxes far beyond the float rounding of the slab test
     const float expand = std::ldexp(c->max_abs, -19);
-    if (lxo::build_bvh(c->tri_v.data(), c->nt, q.leaf_size, q.sah_bins, q.n_threads, expand, &b, msg, sizeof msg))
+    // thin dense layers (electrode wire meshes, PMT arrays) get their own
+    // grid-entered trees
+    std::vector<int32_t> cluster_of(c->nt, -1);
+    const int n_clusters = lxo::detect_layers(c->tri_v.data(), c->nt, cluster_of.data());
+    if (lxo::build_bvh(c->tri_v.data(), c->nt, cluster_of.data(), n_clusters, q.leaf_size, q.sah_bins, q.n_threads,
+                       expand, &b, msg, sizeof msg))
         return fail(c, LXO_ERR_NOMEM, "%s", msg);
     // attributes of each record
     for (uint32_t k = 0; k < b.n_records; ++k) {
@@ -326,27 +335,53 @@ lxo_status lxo_build_bvh(lxo_ctx* c, const lxo_bvh_params* bp, lxo_bvh_info* inf
     DeviceGuard g(c->device);
     free_device_geometry(c);
     const size_t nb = sizeof(float4) * 4ull * b.n_nodes, tb = sizeof(float4) * 3ull * b.n_records;
+    const size_t cb = sizeof(int32_t) * std::max(1u, b.n_cells);
     cudaError_t e = cudaMalloc(&c->d_nodes, nb);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tris, tb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_cells, cb);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_nodes, b.nodes, nb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tris, b.tris, tb, cudaMemcpyHostToDevice);
-    lxo::free_bvh(&b);
+    if (e == cudaSuccess && b.n_cells) e = cudaMemcpy(c->d_cells, b.cells, sizeof(int32_t) * b.n_cells,
+                                                      cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
+        lxo::free_bvh(&b);
         free_device_geometry(c);
         return cuda_fail(c, e, "build_bvh: upload");
     }
+    lxo::Scene& sc = c->scene;
+    sc.nodes = c->d_nodes;
+    sc.tris = c->d_tris;
+    sc.n_tris = c->nt;
+    sc.main_root = b.main_root;
+    sc.n_clusters = b.n_clusters;
+    for (int k = 0; k < b.n_clusters; ++k) {
+        const lxo::ClusterHost& h = b.clusters[k];
+        lxo::ClusterDev& d = sc.clusters[k];
+        d.axis = h.axis;
+        d.nu = h.nu;
+        d.nv = h.nv;
+        d.root = h.root;
+        d.slab_lo = h.slab_lo;
+        d.slab_hi = h.slab_hi;
+        d.u0 = h.u0;
+        d.v0 = h.v0;
+        d.inv_cell = h.inv_cell;
+        d.delta = expand;
+        d.cells = c->d_cells + h.cells_offset;
+    }
+    lxo::free_bvh(&b);
     c->info.n_tris = c->nt;
     c->info.n_nodes = b.n_nodes;
     c->info.n_leaves = b.n_leaves;
     c->info.max_depth = b.max_depth;
-    c->info.node_bytes = nb;
+    c->info.node_bytes = nb + cb;
     c->info.tri_bytes = tb;
     c->info.build_seconds = b.build_seconds;
     c->info.sah_cost = b.sah_cost;
     if (info) *info = c->info;
     c->have_bvh = true;
     c->validated = false;
-    if (b.max_depth >= (uint32_t)lxo::kStackSize)
+    if (b.max_depth + lxo::kMaxClusters * lxo::kMaxCellsPerRay + 1 >= (uint32_t)lxo::kStackSize)
         return fail(c, LXO_ERR_ARG, "build_bvh: depth %u exceeds the traversal stack", b.max_depth);
     return LXO_OK;
 }
@@ -359,8 +394,7 @@ lxo_status lxo_trace_rays(lxo_ctx* c, const float* org, const float* dir, const 
     if (n == 0) return LXO_OK;
     if (!org || !dir || !hit || !t) return fail(c, LXO_ERR_ARG, "trace_rays: NULL array");
     DeviceGuard g(c->device);
-    lxo::Scene sc{c->d_nodes, c->d_tris, c->nt};
-    CK(lxo::launch_trace(sc, org, dir, skip, tmax, n, hit, t, c->d_err, (cudaStream_t)stream), "trace_rays");
+    CK(lxo::launch_trace(c->scene, org, dir, skip, tmax, n, hit, t, c->d_err, (cudaStream_t)stream), "trace_rays");
     return LXO_OK;
 }
 

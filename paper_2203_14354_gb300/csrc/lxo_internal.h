@@ -30,18 +30,49 @@ enum : int { kErrStack = 1, kErrChannel = 2, kErrTimeout = 4 };
 // Triangle record: 48 bytes = 3 float4: (v0.xyz, v1.x), (v1.yz, v2.xy),
 // (v2.z, id, attr, channel) -- id, attr and channel as int bits;
 // attr = mat_inner | mat_outer << 8 | surface << 16.
+// A planar cluster: a large set of triangles confined to a thin slab
+// perpendicular to `axis` (an electrode wire mesh).  It gets its own tree: a
+// kd top split on a 2-D grid of cells (in-plane axes u = axis+1, v = axis+2)
+// over small per-cell sub-trees holding every triangle whose box overlaps the
+// cell.  A ray crossing the slab starts at the sub-trees of the <= 4 cells its
+// in-slab segment touches; other rays fall back to the cluster root.
+constexpr int kMaxClusters = 8;
+constexpr int kMaxCellsPerRay = 4;
+
+struct ClusterHost {
+    int axis;
+    float slab_lo, slab_hi;     // along axis, widened by the box margin
+    float u0, v0, inv_cell;     // grid origin and 1 / cell size
+    int nu, nv;
+    int32_t root;               // reference of the cluster tree root
+    uint32_t cells_offset;      // first cell in BvhHost::cells
+};
+
 struct BvhHost {
     float4* nodes = nullptr;     // host copy [n_nodes * 4]
     float4* tris = nullptr;      // [n_records * 3]
-    uint32_t n_nodes = 0, n_records = 0, n_leaves = 0, max_depth = 0;
+    int32_t* cells = nullptr;    // [n_cells] sub-tree reference per cell (kEmptyChild if empty)
+    uint32_t n_nodes = 0, n_records = 0, n_leaves = 0, max_depth = 0, n_cells = 0;
+    int32_t main_root = kEmptyChild;  // root of the tree over the non-cluster triangles
+    int n_clusters = 0;
+    ClusterHost clusters[kMaxClusters];
     double sah_cost = 0.0, build_seconds = 0.0;
 };
 
-// Builds the BVH from vertex triplets tri_v [nt*9].  expand: absolute
-// widening of every box (conservative traversal).  Returns 0 or -1 (err set).
-int build_bvh(const float* tri_v, uint32_t nt, uint32_t leaf_size, uint32_t bins, uint32_t n_threads,
-              float expand, BvhHost* out, char* err, size_t err_len);
+// Builds the forest from vertex triplets tri_v [nt*9].  cluster_of [nt]: -1
+// for the main tree, else the planar cluster index (< n_clusters <=
+// kMaxClusters); may be NULL.  expand: absolute widening of every box and
+// slab (conservative traversal).  Returns 0 or -1 (err set).
+int build_bvh(const float* tri_v, uint32_t nt, const int32_t* cluster_of, int n_clusters, uint32_t leaf_size,
+              uint32_t bins, uint32_t n_threads, float expand, BvhHost* out, char* err, size_t err_len);
 void free_bvh(BvhHost* b);
+
+// Finds thin dense layers: along each axis, triangles at most 0.4 % of the
+// scene extent thick, grouped while their extents overlap (3 mm tolerance),
+// kept if a group holds >= 32768 triangles within 1 % of the scene extent.
+// Writes cluster_of [nt] (-1 = main tree) and returns the number of layers
+// (largest first, at most kMaxClusters).
+int detect_layers(const float* tri_v, uint32_t nt, int32_t* cluster_of);
 
 struct DevMaterial {
     float n;
@@ -55,10 +86,20 @@ struct DevSurface {
     float R, spec, qe, T, Rw, wspec;
 };
 
+struct ClusterDev {
+    int axis, nu, nv;
+    int32_t root;
+    float slab_lo, slab_hi, u0, v0, inv_cell, delta;
+    const int32_t* cells;  // device [nu * nv], row v * nu + u
+};
+
 struct Scene {
     const float4* nodes;
     const float4* tris;    // records in leaf order
     uint32_t n_tris;
+    int32_t main_root;     // kEmptyChild if every triangle is in a cluster
+    int n_clusters;
+    ClusterDev clusters[kMaxClusters];
 };
 
 struct SourceDev {

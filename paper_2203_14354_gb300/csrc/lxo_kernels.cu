@@ -174,7 +174,14 @@ __device__ __forceinline__ float safe_inv(float d)
 
 struct Counters {
     uint32_t nodes, leaves, tris;
+    uint32_t node_iters, leaf_iters;   // warp iterations of the node / leaf loops (counted by one lane)
+    unsigned long long trav_cycles;     // lane cycles inside the traversal
 };
+
+__device__ __forceinline__ bool warp_leader()
+{
+    return (threadIdx.x & 31u) == (uint32_t)(__ffs(__activemask()) - 1);
+}
 
 // Leaf test of one leaf reference: every triangle of the leaf through the
 // exact watertight test, keeping (t, id) minimal in that order.
@@ -206,36 +213,102 @@ __device__ __forceinline__ void test_leaf(const Scene& sc, const WRay& wr, int r
 
 constexpr int kDone = INT32_MIN + 1;  // stack sentinel; never a valid leaf reference (< 2^28 records)
 
-// "while-while" traversal with postponed leaves (Aila & Laine, HPG 2009): a
-// lane that reaches a leaf parks it and keeps descending until every active
-// lane of the warp holds a leaf; then the warp tests leaves together.  This
-// keeps the node loop and the triangle loop from interleaving divergently.
-template <bool kStats>
-__device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, float tmax, int* err, Counters& cnt)
+// Resumable traversal state of one ray (its stack lives in a separate local
+// array of kStackSize entries).
+struct TravState {
+    WRay wr;
+    float ix, iy, iz, oix, oiy, oiz;
+    uint32_t skip;
+    float bt;
+    uint32_t best, best_rec;
+    int node, leaf, sp;
+    uint32_t nodes0, leaves0;  // counters at the start (counting build only)
+};
+
+// Sets up the closest-hit query of ray (o, d) with t in (0, tmax], skipping
+// triangle `skip`.  Planar clusters: a ray crossing the slab within a few grid
+// cells starts at those cells' sub-trees; any other ray meeting the slab at
+// the cluster root.
+__device__ __forceinline__ void trav_begin(const Scene& sc, float3 o, float3 d, uint32_t skip, float tmax,
+                                           TravState& ts, int* stack)
 {
-    const WRay wr = wray_setup(o, d);
-    const float ix = safe_inv(d.x), iy = safe_inv(d.y), iz = safe_inv(d.z);
-    const float oix = o.x * ix, oiy = o.y * iy, oiz = o.z * iz;
-    uint32_t best = LXO_NO_HIT, best_rec = 0;
-    float bt = tmax;
-    int stack[kStackSize];
+    ts.wr = wray_setup(o, d);
+    ts.ix = safe_inv(d.x);
+    ts.iy = safe_inv(d.y);
+    ts.iz = safe_inv(d.z);
+    ts.oix = o.x * ts.ix;
+    ts.oiy = o.y * ts.iy;
+    ts.oiz = o.z * ts.iz;
+    ts.skip = skip;
+    ts.bt = tmax;
+    ts.best = LXO_NO_HIT;
+    ts.best_rec = 0;
     stack[0] = kDone;
     int sp = 1;
-    int node = 0;   // root
-    int leaf = 0;   // parked leaf (0 = none: reference 0 is the root, never a leaf)
-    while (node != kDone) {
+    for (int c = 0; c < sc.n_clusters; ++c) {
+        const ClusterDev& cl = sc.clusters[c];
+        const float oa = pick(cl.axis, o.x, o.y, o.z), ia = pick(cl.axis, ts.ix, ts.iy, ts.iz);
+        const float ta = (cl.slab_lo - oa) * ia, tb = (cl.slab_hi - oa) * ia;
+        const float tin = fmaxf(fminf(ta, tb), 0.0f), tout = fminf(fmaxf(ta, tb), tmax * kBoxSlack);
+        if (!(tin <= tout)) continue;
+        if (tout < 1e30f) {
+            const int bu = cl.axis == 2 ? 0 : cl.axis + 1;   // in-plane axes (axis+1, axis+2) mod 3
+            const int bv = cl.axis == 0 ? 2 : cl.axis - 1;
+            const float ou = pick(bu, o.x, o.y, o.z), du = pick(bu, d.x, d.y, d.z);
+            const float ov = pick(bv, o.x, o.y, o.z), dv = pick(bv, d.x, d.y, d.z);
+            const float u1 = ou + tin * du, u2 = ou + tout * du, v1 = ov + tin * dv, v2 = ov + tout * dv;
+            const float fi0 = fmaxf(floorf((fminf(u1, u2) - cl.delta - cl.u0) * cl.inv_cell), 0.0f);
+            const float fi1 = fminf(floorf((fmaxf(u1, u2) + cl.delta - cl.u0) * cl.inv_cell), (float)(cl.nu - 1));
+            const float fj0 = fmaxf(floorf((fminf(v1, v2) - cl.delta - cl.v0) * cl.inv_cell), 0.0f);
+            const float fj1 = fminf(floorf((fmaxf(v1, v2) + cl.delta - cl.v0) * cl.inv_cell), (float)(cl.nv - 1));
+            if (!(fi0 <= fi1) || !(fj0 <= fj1)) continue;  // outside the cluster's grid
+            if ((fi1 - fi0 + 1.0f) * (fj1 - fj0 + 1.0f) <= (float)kMaxCellsPerRay) {
+                for (int j = (int)fj0; j <= (int)fj1; ++j)
+                    for (int i = (int)fi0; i <= (int)fi1; ++i) {
+                        const int r = __ldg(&cl.cells[(size_t)j * cl.nu + i]);
+                        if (r != kEmptyChild) stack[sp++] = r;
+                    }
+                continue;
+            }
+        }
+        stack[sp++] = cl.root;
+    }
+    ts.node = sc.main_root != kEmptyChild ? sc.main_root : stack[--sp];
+    ts.leaf = 0;  // parked leaf (0 = none: reference 0 is an internal node, never a leaf)
+    ts.sp = sp;
+}
+
+// "While-while" traversal with postponed leaves (Aila & Laine, HPG 2009): a
+// lane that reaches a leaf parks it and keeps descending until every active
+// lane of the warp holds a leaf; then the warp tests leaves together.
+// Returns true when the query is complete.  With phys_min <= 32 it also
+// returns false (state saved, resumable) as soon as at least phys_min lanes
+// of the warp are no longer traversing, so that their photons can be
+// advanced together.
+template <bool kStats>
+__device__ bool trav_run(const Scene& sc, TravState& ts, int* stack, int* err, Counters& cnt, int phys_min)
+{
+    int node = ts.node, leaf = ts.leaf, sp = ts.sp;
+    float bt = ts.bt;
+    uint32_t best = ts.best, best_rec = ts.best_rec;
+    bool done = false;
+    while (true) {
+        bool yield = false;
         while (node >= 0) {
-            if (kStats) cnt.nodes++;
+            if (kStats) {
+                cnt.nodes++;
+                if (warp_leader()) cnt.node_iters++;
+            }
             const float4* nd = sc.nodes + 4 * (size_t)node;
             const float4 nx = __ldg(nd + 0), ny = __ldg(nd + 1), nz = __ldg(nd + 2);
             const int4 cr = __ldg(reinterpret_cast<const int4*>(nd + 3));
             const float lim = bt * kBoxSlack;
-            const float ax0 = fmaf(nx.x, ix, -oix), ax1 = fmaf(nx.y, ix, -oix);
-            const float ay0 = fmaf(ny.x, iy, -oiy), ay1 = fmaf(ny.y, iy, -oiy);
-            const float az0 = fmaf(nz.x, iz, -oiz), az1 = fmaf(nz.y, iz, -oiz);
-            const float bx0 = fmaf(nx.z, ix, -oix), bx1 = fmaf(nx.w, ix, -oix);
-            const float by0 = fmaf(ny.z, iy, -oiy), by1 = fmaf(ny.w, iy, -oiy);
-            const float bz0 = fmaf(nz.z, iz, -oiz), bz1 = fmaf(nz.w, iz, -oiz);
+            const float ax0 = fmaf(nx.x, ts.ix, -ts.oix), ax1 = fmaf(nx.y, ts.ix, -ts.oix);
+            const float ay0 = fmaf(ny.x, ts.iy, -ts.oiy), ay1 = fmaf(ny.y, ts.iy, -ts.oiy);
+            const float az0 = fmaf(nz.x, ts.iz, -ts.oiz), az1 = fmaf(nz.y, ts.iz, -ts.oiz);
+            const float bx0 = fmaf(nx.z, ts.ix, -ts.oix), bx1 = fmaf(nx.w, ts.ix, -ts.oix);
+            const float by0 = fmaf(ny.z, ts.iy, -ts.oiy), by1 = fmaf(ny.w, ts.iy, -ts.oiy);
+            const float bz0 = fmaf(nz.z, ts.iz, -ts.oiz), bz1 = fmaf(nz.w, ts.iz, -ts.oiz);
             const float an = fmaxf(fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)), fmaxf(fminf(az0, az1), 0.0f));
             const float af = fminf(fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)), fminf(fmaxf(az0, az1), lim));
             const float bn = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), 0.0f));
@@ -261,18 +334,55 @@ __device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, f
                 leaf = node;
                 node = stack[--sp];
             }
-            if (!__any_sync(__activemask(), leaf == 0)) break;
+            const uint32_t am = __activemask();
+            if (!__any_sync(am, leaf == 0)) break;
+            if (32 - __popc(am) >= phys_min) {
+                yield = true;
+                break;
+            }
+        }
+        if (yield) break;
+        if (node < 0 && node != kDone && leaf == 0) {  // a leaf reference taken from the stack
+            leaf = node;
+            node = stack[--sp];
         }
         while (leaf != 0) {
-            test_leaf<kStats>(sc, wr, leaf, skip, bt, best, best_rec, cnt);
+            if (kStats && warp_leader()) cnt.leaf_iters++;
+            test_leaf<kStats>(sc, ts.wr, leaf, ts.skip, bt, best, best_rec, cnt);
             leaf = 0;
             if (node < 0 && node != kDone) {
                 leaf = node;
                 node = stack[--sp];
             }
         }
+        if (node == kDone) {
+            done = true;
+            break;
+        }
+        if (32 - __popc(__activemask()) >= phys_min) break;
     }
-    return Hit{best, best_rec, best == LXO_NO_HIT ? INFINITY : bt};
+    ts.node = node;
+    ts.leaf = leaf;
+    ts.sp = sp;
+    ts.bt = bt;
+    ts.best = best;
+    ts.best_rec = best_rec;
+    return done;
+}
+
+__device__ __forceinline__ Hit trav_result(const TravState& ts)
+{
+    return Hit{ts.best, ts.best_rec, ts.best == LXO_NO_HIT ? INFINITY : ts.bt};
+}
+
+template <bool kStats>
+__device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, float tmax, int* err, Counters& cnt)
+{
+    TravState ts;
+    int stack[kStackSize];
+    trav_begin(sc, o, d, skip, tmax, ts, stack);
+    trav_run<kStats>(sc, ts, stack, err, cnt, 33);
+    return trav_result(ts);
 }
 
 __global__ void k_trace(const Scene sc, const float* __restrict__ org, const float* __restrict__ dir,
@@ -283,7 +393,7 @@ __global__ void k_trace(const Scene sc, const float* __restrict__ org, const flo
     if (i >= n) return;
     const float3 o = f3(org[3 * i], org[3 * i + 1], org[3 * i + 2]);
     const float3 d = f3(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]);
-    Counters cnt{0, 0, 0};
+    Counters cnt{};
     const Hit h = closest_hit<false>(sc, o, d, skip ? skip[i] : LXO_NO_HIT, tmax ? tmax[i] : INFINITY, err, cnt);
     hit[i] = h.id;
     t[i] = h.t;
@@ -497,15 +607,41 @@ __device__ __forceinline__ void spawn_offset(Photon& ph, float3 o_ray, float t_h
 
 // one interaction; returns -1 if the photon lives on, else its fate code
 // (detail set to channel / material / surface / triangle)
-template <bool kStats>
-__device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counters& cnt)
+// First half of a step: the step's uniforms and the absorption / Rayleigh
+// distances in the current medium.
+struct StepDraw {
+    float d_abs, d_ray, u2, u3;
+};
+
+__device__ __forceinline__ StepDraw begin_step(const PropParams& p, const Photon& ph)
 {
     const U4 u = draw4(p.seed, ph.pid, ph.step, 0);
     const DevMaterial& mt = p.mat[ph.medium];
-    const float d_abs = isinf(mt.abs_len) ? INFINITY : -mt.abs_len * logf(u.u0);
-    const float d_ray = isinf(mt.ray_len) ? INFINITY : -mt.ray_len * logf(u.u1);
-    const float d_int = fminf(d_abs, d_ray);
-    const Hit h = closest_hit<kStats>(p.sc, ph.pos, ph.dir, ph.last, d_int, p.err, cnt);
+    StepDraw sd;
+    sd.d_abs = isinf(mt.abs_len) ? INFINITY : -mt.abs_len * logf(u.u0);
+    sd.d_ray = isinf(mt.ray_len) ? INFINITY : -mt.ray_len * logf(u.u1);
+    sd.u2 = u.u2;
+    sd.u3 = u.u3;
+    return sd;
+}
+
+template <bool kStats>
+__device__ __forceinline__ void step_histogram(const PropParams& p, const Photon& ph, uint32_t dn, uint32_t dl)
+{
+    // per-step histogram of node visits (8-wide bins) split by medium (0 vs other), and leaves
+    const int m = ph.medium == 0 ? 0 : 1;
+    atomicAdd(&p.out.stats[9 + 10 * m + min(dn / 8u, 8u)], 1ull);
+    atomicAdd(&p.out.stats[9 + 10 * m + 9], (unsigned long long)dl);
+}
+
+// Second half of a step: the interaction at the closest hit or in the bulk.
+// Returns -1 if the photon lives on, else its fate code (detail set to
+// channel / material / surface / triangle).
+__device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, const Hit& h, int& detail)
+{
+    const float d_abs = sd.d_abs, d_ray = sd.d_ray, d_int = fminf(d_abs, d_ray);
+    const U4 u = U4{0.0f, 0.0f, sd.u2, sd.u3};
+    const DevMaterial& mt = p.mat[ph.medium];
     if (h.id == LXO_NO_HIT) {
         if (isinf(d_int)) {
             detail = -1;
@@ -596,19 +732,34 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
     return -1;
 }
 
+// one whole interaction (draw, closest hit, interaction)
+template <bool kStats>
+__device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counters& cnt)
+{
+    const StepDraw sd = begin_step(p, ph);
+    const long long c0 = kStats ? clock64() : 0;
+    const uint32_t n0 = kStats ? cnt.nodes : 0, l0 = kStats ? cnt.leaves : 0;
+    const Hit h = closest_hit<kStats>(p.sc, ph.pos, ph.dir, ph.last, fminf(sd.d_abs, sd.d_ray), p.err, cnt);
+    if (kStats) {
+        cnt.trav_cycles += (unsigned long long)(clock64() - c0);
+        step_histogram<kStats>(p, ph, cnt.nodes - n0, cnt.leaves - l0);
+    }
+    return finish_step(p, ph, sd, h, detail);
+}
+
 // ---------------------------------------------------------------------------
 // persistent propagation kernel
 // ---------------------------------------------------------------------------
 constexpr int kPropThreads = 256;
 constexpr uint32_t kChunk = 64;
 // tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
-// idle; 4 CTAs of 256 threads per SM (64 registers) hides more L1/L2 latency
-// than 3 CTAs at 80 registers
+// idle; 5 CTAs of 256 threads per SM (51 registers) hide more L1/L2 latency
+// than 3 CTAs at 80 registers (+22 %) despite a few spills
 #ifndef LXO_REFILL_MIN
 #define LXO_REFILL_MIN 1
 #endif
 #ifndef LXO_MIN_BLOCKS
-#define LXO_MIN_BLOCKS 4
+#define LXO_MIN_BLOCKS 5
 #endif
 
 // Tally of one photon's fate: shared-memory fate counters, global per-channel
@@ -645,8 +796,9 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
 template <bool kStats>
 __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(const __grid_constant__ PropParams p)
 {
-    Counters cnt{0, 0, 0};
-    uint32_t my_steps = 0;
+    Counters cnt{};
+    uint32_t my_steps = 0, outer_iters = 0;
+    unsigned long long loop_cycles = 0;
     __shared__ unsigned long long s_f[kMaxFates];
     for (int i = threadIdx.x; i < p.n_fates; i += blockDim.x) s_f[i] = 0ull;
     __syncthreads();
@@ -691,6 +843,8 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
             }
         }
         if (!__any_sync(FULL_MASK, alive || pending)) break;
+        if (kStats && lane == 0) outer_iters++;
+        const long long c0 = kStats ? clock64() : 0;
         if (alive) {
             fate = photon_step<kStats>(p, ph, detail, cnt);
             ph.step++;
@@ -701,6 +855,7 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
                 pending = true;
             }
         }
+        if (kStats) loop_cycles += (unsigned long long)(clock64() - c0);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < p.n_fates; i += blockDim.x)
@@ -710,6 +865,11 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
         atomicAdd(&p.out.stats[1], (unsigned long long)cnt.nodes);
         atomicAdd(&p.out.stats[2], (unsigned long long)cnt.leaves);
         atomicAdd(&p.out.stats[3], (unsigned long long)cnt.tris);
+        atomicAdd(&p.out.stats[4], (unsigned long long)cnt.node_iters);
+        atomicAdd(&p.out.stats[5], (unsigned long long)cnt.leaf_iters);
+        atomicAdd(&p.out.stats[6], (unsigned long long)outer_iters);
+        atomicAdd(&p.out.stats[7], cnt.trav_cycles);
+        atomicAdd(&p.out.stats[8], loop_cycles);
     }
 }
 
@@ -741,16 +901,13 @@ cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
     const bool stats = (p.flags & LXO_FLAG_STATS) != 0;
-    e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<true>, kPropThreads, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<false>, kPropThreads, 0);
+    auto kern = stats ? k_propagate<true> : k_propagate<false>;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPropThreads, 0);
     if (e != cudaSuccess) return e;
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
     const uint64_t need = (p.n + kPropThreads - 1) / kPropThreads;
     if (need < blocks) blocks = need;
-    if (stats)
-        k_propagate<true><<<(unsigned)blocks, kPropThreads, 0, st>>>(p);
-    else
-        k_propagate<false><<<(unsigned)blocks, kPropThreads, 0, st>>>(p);
+    kern<<<(unsigned)blocks, kPropThreads, 0, st>>>(p);
     return cudaGetLastError();
 }
 

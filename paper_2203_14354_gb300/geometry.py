@@ -216,6 +216,42 @@ def _fan(poly2, z, center2=None):
     return tri
 
 
+def _disk(center2, r, k_seg, z, rings=4):
+    """Disk of radius r as concentric rings (vertex counts k_seg * j / rings)
+    around a small central fan: triangles of bounded aspect ratio instead of
+    k_seg wedges meeting at the centre.  The rim is ``_circle(center2, r,
+    k_seg)``, so it welds to any other primitive sharing that circle."""
+    rings = max(1, min(rings, k_seg // 4))
+    prev = _circle(center2, r / rings, max(4, k_seg // rings))
+    tri = [_fan(prev, z, center2)]
+    for j in range(2, rings + 1):
+        cur = _circle(center2, r * j / rings, max(4, k_seg * j // rings))
+        tri.append(_ring(cur, prev, z, center2))
+        prev = cur
+    return np.concatenate(tri)
+
+
+def _subdivide(poly2, seg_len):
+    """Polygon with every edge split into equal pieces no longer than
+    seg_len; the split points of an edge depend only on its two endpoints
+    (taken in a fixed order), so neighbouring polygons sharing the edge get
+    identical points."""
+    out = []
+    m = len(poly2)
+    for k in range(m):
+        a, b = poly2[k], poly2[(k + 1) % m]
+        out.append(a)
+        L = float(np.hypot(*(b - a)))
+        n = max(1, int(math.ceil(L / seg_len - 1e-9)))
+        swap = tuple(a) > tuple(b)
+        p, q = (b, a) if swap else (a, b)
+        pts = [p + (q - p) * (i / n) for i in range(1, n)]
+        if swap:
+            pts = pts[::-1]
+        out.extend(pts)
+    return np.array(out, np.float64)
+
+
 def _ring(outer2, inner2, z, center2):
     """Triangulate the region between a star-shaped outer polygon and an inner
     polygon (both around ``center2``) by merging their vertices by angle."""
@@ -324,7 +360,7 @@ def hex_lattice(pitch, extent):
 # ----------------------------------------------------------------------------
 # detector parts
 # ----------------------------------------------------------------------------
-def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_plate):
+def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_plate, subdivide=False):
     """PTFE plate at ``z_plate`` filling the wall polygon, with a circular hole
     of radius ``r_window`` at every hex-lattice site whose window fits inside
     the wall.  ``facing`` = +1 if the plate faces up (bottom array), -1 if it
@@ -336,10 +372,14 @@ def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_p
     hexagon = polygon_vertices(6, pitch / math.sqrt(3), math.pi / 6)  # flat-to-flat = pitch
     pmts, cells = [], []
     normal = (0.0, 0.0, -float(facing))  # plate normal points from Xe into PTFE
+    seg_len = 2.0 * math.pi * r_window / k_seg   # the rim's segment length
     for c, pm in zip(centres, has_pmt):
         cell = _clip_convex(hexagon + c, wall2)
         if cell.shape[0] < 3:
             continue
+        # snap before subdividing so that cells sharing an edge split it alike
+        if subdivide:
+            cell = _subdivide(_snap(cell), seg_len)
         cells.append(cell)
         if pm:
             rim = _circle(c, r_window, k_seg)
@@ -351,7 +391,7 @@ def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_p
 
 
 def _pmt_windows(b, centres, z_front, thickness, facing, r_window, r_pc, k_seg, mat_xe,
-                 surf_cap, surf_pc, chan0):
+                 surf_cap, surf_pc, chan0, rings=2):
     """Quartz windows: front face in the xenon (bare dielectric boundary), side
     wall and back-face annulus covered by the absorbing cap, photocathode disk
     of radius ``r_pc`` on the back face (Sec. 2.1, Fig. 1)."""
@@ -359,7 +399,7 @@ def _pmt_windows(b, centres, z_front, thickness, facing, r_window, r_pc, k_seg, 
     for p, c in enumerate(centres):
         rim = _circle(c, r_window, k_seg)
         # front face, normal out of the quartz into the xenon
-        b.add(_fan(rim, z_front, c), (0, 0, facing), QUARTZ, mat_xe)
+        b.add(_disk(c, r_window, k_seg, z_front, rings), (0, 0, facing), QUARTZ, mat_xe)
         # side wall
         r0 = np.concatenate([rim, np.full((k_seg, 1), z_front)], 1)
         r1 = np.concatenate([rim, np.full((k_seg, 1), z_back)], 1)
@@ -373,10 +413,10 @@ def _pmt_windows(b, centres, z_front, thickness, facing, r_window, r_pc, k_seg, 
         # back face: photocathode disk (+ cap annulus)
         back_n = (0, 0, -facing)
         if r_pc >= r_window:
-            b.add(_fan(rim, z_back, c), back_n, QUARTZ, OPAQUE, surf_pc, chan0 + p)
+            b.add(_disk(c, r_window, k_seg, z_back, rings), back_n, QUARTZ, OPAQUE, surf_pc, chan0 + p)
         else:
             inner = _circle(c, r_pc, k_seg)
-            b.add(_fan(inner, z_back, c), back_n, QUARTZ, OPAQUE, surf_pc, chan0 + p)
+            b.add(_disk(c, r_pc, k_seg, z_back, rings), back_n, QUARTZ, OPAQUE, surf_pc, chan0 + p)
             b.add(_ring(rim, inner, z_back, c), back_n, QUARTZ, OPAQUE, surf_cap)
 
 
@@ -427,7 +467,7 @@ def _boundary_points(cells, wall2, tol=1e-6):
                 L = math.hypot(*d)
                 dist = abs(d[0] * (p[1] - a[1]) - d[1] * (p[0] - a[0])) / L
                 s = ((p - a) @ d) / (L * L)
-                if dist < tol * max(1.0, L) and 1e-9 < s < 1 - 1e-9:
+                if dist < max(tol * max(1.0, L), 2.0 / SNAP) and 1e-9 < s < 1 - 1e-9:
                     key = tuple(np.round(p * SNAP).astype(np.int64))
                     if key not in seen[k]:
                         seen[k].add(key)
@@ -512,7 +552,7 @@ def small_tpc(r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe
     LXe under a 5 mm GXe gap, 7 top + 7 bottom hex-packed PMT windows (64 mm
     diameter at 66 mm pitch, photocathode = whole back face; a 7-hex of 3-inch
     windows does not fit in 100 mm radius), Lambertian PTFE 0.95 (LXe) / 0.70
-    (GXe), QE 0.3.  ~3.5k triangles.  Source: uniform in the LXe, isotropic."""
+    (GXe), QE 0.3.  ~4.4k triangles.  Source: uniform in the LXe, isotropic."""
     R, z_bot, z_liq, z_top = 100.0, -100.0, 0.0, 5.0
     r_w, pitch, thick = 32.0, 66.0, 5.0
     mats = default_materials(lxe_abs_mm, lxe_ray_mm)
@@ -530,8 +570,8 @@ def small_tpc(r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe
     _wall(b, wall2, z_bot, z_liq, LXE, S_PTFE_L, bottom_pts=bot_edge)
     _wall(b, wall2, z_liq, z_top, GXE, S_PTFE_G, top_pts=top_edge)
     b.add(_fan(wall2, z_liq, (0, 0)), (0, 0, 1), LXE, GXE)           # liquid surface
-    _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_w, k_seg, LXE, S_CAP, S_PC, 0)
-    _pmt_windows(b, top, z_top, thick, -1, r_w, r_w, k_seg, GXE, S_CAP, S_PC, len(bot))
+    _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_w, k_seg, LXE, S_CAP, S_PC, 0, rings=2)
+    _pmt_windows(b, top, z_top, thick, -1, r_w, r_w, k_seg, GXE, S_CAP, S_PC, len(bot), rings=2)
     src = Source(SRC_VOLUME_POLYGON, LXE, n_sides=wall_sides, radius=R, z_min=z_bot, z_max=z_liq)
     return _detector("small_tpc", b, mats, surfs, bot, top, z_bot - thick, z_top + thick, src,
                      dict(radius=R, wall_sides=wall_sides, z_liquid=z_liq))
@@ -539,7 +579,7 @@ def small_tpc(r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe
 
 def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "anode", "cathode"),
            r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe_ray_mm=400.0,
-           r_ss=0.30, ss_spec_frac=2.0 / 3.0, k_seg=32, active_only=True):
+           r_ss=0.30, ss_spec_frac=2.0 / 3.0, k_seg=32, active_only=True, window_rings=2, plate_subdivide=False):
     """DARWIN-scale dual-phase TPC (Sec. 2.1, Table 1): 24-sided PTFE wall
     inscribed in r = 1300 mm; gate z = 0 (LXe), liquid surface z = +2, anode
     z = +8 (GXe), cathode z = -2598; hex-packed 3-inch windows (76.2 mm, 5 mm
@@ -562,13 +602,13 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
     ]
     wall2 = polygon_vertices(24, R)
     b = _Builder()
-    bot, bot_edge = _pmt_plate(b, wall2, z_bot, pitch_pmt, r_w, k_seg, +1, LXE, S_PTFE_L)
-    top, top_edge = _pmt_plate(b, wall2, z_top, pitch_pmt, r_w, k_seg, -1, GXE, S_PTFE_G)
+    bot, bot_edge = _pmt_plate(b, wall2, z_bot, pitch_pmt, r_w, k_seg, +1, LXE, S_PTFE_L, plate_subdivide)
+    top, top_edge = _pmt_plate(b, wall2, z_top, pitch_pmt, r_w, k_seg, -1, GXE, S_PTFE_G, plate_subdivide)
     _wall(b, wall2, z_bot, z_liq, LXE, S_PTFE_L, bottom_pts=bot_edge)
     _wall(b, wall2, z_liq, z_top, GXE, S_PTFE_G, top_pts=top_edge)
     b.add(_fan(wall2, z_liq, (0, 0)), (0, 0, 1), LXE, GXE)
-    _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_pc, k_seg, LXE, S_CAP, S_PC, 0)
-    _pmt_windows(b, top, z_top, thick, -1, r_w, r_pc, k_seg, GXE, S_CAP, S_PC, len(bot))
+    _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_pc, k_seg, LXE, S_CAP, S_PC, 0, rings=window_rings)
+    _pmt_windows(b, top, z_top, thick, -1, r_w, r_pc, k_seg, GXE, S_CAP, S_PC, len(bot), rings=window_rings)
     zs = dict(gate=(z_gate, LXE), anode=(z_anode, GXE), cathode=(z_cath, LXE))
     for name in electrodes:
         ze, mat = zs[name]

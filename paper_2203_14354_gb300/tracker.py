@@ -170,11 +170,11 @@ class Tracker:
         """Propagates photons base..base+n-1; returns (accumulates into) a dict
         of device tensors: lce, det [P], hist [P, n_tbins+1], fates [8+M+S]
         and, with per_photon, fate / detail / steps / time [n]; with stats,
-        stats [4] = steps, nodes visited, leaves visited, triangles tested."""
+        stats [32] as documented for lxo_results.stats in include/lxo.h."""
         if out is None:
             out = self.alloc_results(n_tbins, n if per_photon else 0)
         if stats and "stats" not in out:
-            out["stats"] = torch.zeros(4, dtype=torch.int64, device=self.device)
+            out["stats"] = torch.zeros(32, dtype=torch.int64, device=self.device)
         src = make_source(source or self.det.source, explicit)
         if explicit is not None and src.kind != SRC_EXPLICIT:
             raise ValueError("explicit arrays need an SRC_EXPLICIT source")
