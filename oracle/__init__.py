@@ -57,6 +57,9 @@ def lib():
         L.orc_propagate.restype = C.c_int
         L.orc_propagate.argtypes = [C.c_void_p, C.POINTER(_Source), C.c_uint64, C.c_uint64, C.c_uint64,
                                     C.c_uint32, C.c_double, C.c_uint32, C.POINTER(_Results), C.c_int]
+        L.orc_set_adjoint.restype = C.c_int
+        L.orc_set_adjoint.argtypes = [C.c_void_p, i32p, C.c_int, i32p, C.c_int]
+        L.orc_jacobian.argtypes = [C.c_void_p, f64p, f64p]
         L.orc_philox.argtypes = [u32p, u32p, u32p]
         L.orc_uniform.restype = C.c_double
         L.orc_uniform.argtypes = [C.c_uint32]
@@ -102,6 +105,29 @@ class Oracle:
                            x.wire_spec_frac] for x in det.surfaces], np.float64).ravel()
             assert L.orc_set_surfaces(self._s, t, p, self.n_surf) == 0
         L.orc_set_channels(self._s, self.n_chan)
+        self.adj_mats, self.adj_surfs = [], []
+
+    def set_adjoint(self, mats=(), surfs=()):
+        """Track (L_abs, L_ray) of materials `mats` and R or T of surfaces `surfs`."""
+        m = np.ascontiguousarray(list(mats) or [0], np.int32)
+        sf = np.ascontiguousarray(list(surfs) or [0], np.int32)
+        if lib().orc_set_adjoint(self._s, m, len(mats), sf, len(surfs)) != 0:
+            raise ValueError("bad adjoint spec")
+        self.adj_mats, self.adj_surfs = list(mats), list(surfs)
+
+    @property
+    def n_tallies(self):
+        return 2 * len(self.adj_mats) + 2 * len(self.adj_surfs)
+
+    @property
+    def n_params(self):
+        return 2 * len(self.adj_mats) + len(self.adj_surfs)
+
+    def jacobian(self, sums):
+        sums = np.ascontiguousarray(sums, np.float64).reshape(self.n_chan, self.n_tallies)
+        J = np.zeros((self.n_chan, self.n_params))
+        lib().orc_jacobian(self._s, sums, J)
+        return J
 
     def __del__(self):
         if getattr(self, "_s", None) and _lib is not None:
@@ -138,7 +164,7 @@ class Oracle:
         return pos, dir, pol, med
 
     def propagate(self, n, base=0, seed=0, src=None, explicit=None, max_steps=10000, tbin_ns=1.0,
-                  n_tbins=1000, per_photon=False, threads=None):
+                  n_tbins=1000, per_photon=False, threads=None, adjoint=False):
         s, keep = self._source(src or self.det.source, explicit)
         P = self.n_chan
         out = dict(lce=np.zeros(P, np.uint64), det=np.zeros(P, np.uint64),
@@ -147,11 +173,15 @@ class Oracle:
         if per_photon:
             out.update(fate=np.zeros(n, np.uint32), detail=np.zeros(n, np.int32),
                        steps=np.zeros(n, np.uint32), time=np.zeros(n, np.float32))
+        if adjoint:
+            out["adjoint"] = np.zeros((P, self.n_tallies), np.float64)
         r = _Results()
         r.lce, r.det, r.hist, r.fates = _ptr(out["lce"]), _ptr(out["det"]), _ptr(out["hist"]), _ptr(out["fates"])
         if per_photon:
             r.ph_fate, r.ph_detail = _ptr(out["fate"]), _ptr(out["detail"])
             r.ph_steps, r.ph_time = _ptr(out["steps"]), _ptr(out["time"])
+        if adjoint:
+            r.adjoint = _ptr(out["adjoint"])
         if threads is None:
             threads = os.cpu_count() or 1
         rc = lib().orc_propagate(self._s, C.byref(s), n, base, seed, max_steps, tbin_ns, n_tbins, C.byref(r),

@@ -44,6 +44,8 @@ struct orc_scene {
     int stype[256];
     double sp[256][6];
     int n_chan;
+    int n_amat, amat[4], n_asurf, asurf[8];
+    int mat_slot[64], surf_slot[256];  /* tracked index or -1 */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -301,6 +303,8 @@ orc_scene* orc_scene_new(const float* verts, uint32_t nv, const uint32_t* tris, 
     for (uint32_t i = 0; i < nt; ++i) s->order[i] = refs[i].id;
     free(refs);
     s->n_chan = 0;
+    for (int i = 0; i < 64; ++i) s->mat_slot[i] = -1;
+    for (int i = 0; i < 256; ++i) s->surf_slot[i] = -1;
     return s;
 }
 
@@ -335,6 +339,56 @@ int orc_set_channels(orc_scene* s, int n_channels)
 {
     s->n_chan = n_channels;
     return 0;
+}
+
+int orc_set_adjoint(orc_scene* s, const int* mats, int n_mats, const int* surfs, int n_surfs)
+{
+    if (n_mats < 0 || n_mats > 4 || n_surfs < 0 || n_surfs > 8) return -1;
+    for (int i = 0; i < 64; ++i) s->mat_slot[i] = -1;
+    for (int i = 0; i < 256; ++i) s->surf_slot[i] = -1;
+    for (int i = 0; i < n_mats; ++i) {
+        if (mats[i] < 0 || mats[i] >= 64) return -1;
+        s->amat[i] = mats[i];
+        s->mat_slot[mats[i]] = i;
+    }
+    for (int j = 0; j < n_surfs; ++j) {
+        if (surfs[j] < 0 || surfs[j] >= 256) return -1;
+        s->asurf[j] = surfs[j];
+        s->surf_slot[surfs[j]] = j;
+    }
+    s->n_amat = n_mats;
+    s->n_asurf = n_surfs;
+    return 0;
+}
+
+/* Score of a detected path (the photon never was absorbed):
+ *  bulk absorption over length l in material of absorption length L: exp(-l/L)
+ *    -> d/dL log = l / L^2
+ *  Rayleigh: N scatters over length l: L^-N exp(-l/L) -> d/dL log = l/L^2 - N/L
+ *  each reflection on a reflector of reflectivity R: factor R -> n / R
+ *  electrode of transparency T: T per pass, (1-T) R_w per wire reflection
+ *    -> n_T / T - n_W / (1 - T) */
+void orc_jacobian(const orc_scene* s, const double* sums, double* J)
+{
+    const int K = 2 * s->n_amat + 2 * s->n_asurf, Q = 2 * s->n_amat + s->n_asurf;
+    for (int c = 0; c < s->n_chan; ++c) {
+        const double* t = &sums[(size_t)c * K];
+        double* j = &J[(size_t)c * Q];
+        for (int i = 0; i < s->n_amat; ++i) {
+            const double La = s->mat[s->amat[i]][1], Lr = s->mat[s->amat[i]][2];
+            j[2 * i] = isinf(La) ? 0.0 : t[2 * i] / (La * La);
+            j[2 * i + 1] = isinf(Lr) ? 0.0 : t[2 * i] / (Lr * Lr) - t[2 * i + 1] / Lr;
+        }
+        for (int q = 0; q < s->n_asurf; ++q) {
+            const int sid = s->asurf[q];
+            const double* sp = s->sp[sid];
+            const double a = t[2 * s->n_amat + 2 * q], b = t[2 * s->n_amat + 2 * q + 1];
+            double g = 0.0;
+            if (s->stype[sid] == ORC_REFLECTOR) g = a / sp[0];
+            else if (s->stype[sid] == ORC_ELECTRODE_T) g = a / sp[3] - b / (1.0 - sp[3]);
+            j[2 * s->n_amat + q] = g;
+        }
+    }
 }
 
 /* slab test in double against a box widened by 1e-3 mm */
@@ -660,6 +714,8 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
     int32_t detail = -1;
     uint32_t step;
     const int M = s->n_mat;
+    double tl[24] = {0};  /* adjoint tallies of this photon */
+    const int na = s->n_amat;
     for (step = 0; step < max_steps; ++step) {
         double u[4];
         draw4(seed, pid, step, 0, u);
@@ -673,11 +729,14 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
         float th;
         uint32_t tri = closest_hit(s, of, df, last, tmax, &th, 0);
         double vel = C_MM_PER_NS / mat[0];
+        const int ms = s->mat_slot[medium];
         if (tri == NO_HIT) {
             if (isinf(d_int)) { fate = ORC_ESCAPED; detail = -1; break; }
             for (int a = 0; a < 3; ++a) pos[a] += d_int * dir[a];
             time += d_int / vel;
+            if (ms >= 0) tl[2 * ms] += d_int;
             if (d_abs <= d_ray) { fate = ORC_BULK_ABS; detail = medium; break; }
+            if (ms >= 0) tl[2 * ms + 1] += 1.0;
             double k2[3], e2[3];
             orc_rayleigh(dir, pol, pid, step, seed, k2, e2);
             memcpy(dir, k2, sizeof k2);
@@ -689,6 +748,7 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
         double o_ray[3] = {pos[0], pos[1], pos[2]};
         for (int a = 0; a < 3; ++a) pos[a] += (double)th * dir[a];
         time += (double)th / vel;
+        if (ms >= 0) tl[2 * ms] += (double)th;
         const float* v = &s->v[9ull * tri];
         double e1[3] = {(double)v[3] - v[0], (double)v[4] - v[1], (double)v[5] - v[2]};
         double e2v[3] = {(double)v[6] - v[0], (double)v[7] - v[1], (double)v[8] - v[2]};
@@ -715,6 +775,7 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
         }
         int type = s->stype[sid];
         const double* sp = s->sp[sid];
+        const int ss = s->surf_slot[sid];
         if (type == ORC_ABSORBER) { fate = ORC_SURF_ABS; detail = sid; break; }
         if (type == ORC_PHOTOCATHODE) {
             int c = s->ch[tri];
@@ -726,15 +787,18 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
         int reflect_specular = -1; /* -1: no reflection */
         if (type == ORC_REFLECTOR) {
             if (!(u[2] < sp[0])) { fate = ORC_SURF_ABS; detail = sid; break; }
+            if (ss >= 0) tl[2 * na + 2 * ss] += 1.0;
             reflect_specular = u[3] < sp[1];
         } else if (type == ORC_ELECTRODE_T) {
             if (u[2] < sp[3]) { /* passes between the wires */
                 if (from != medium || to >= M) { fate = ORC_GEOM_ERR; detail = (int32_t)tri; break; }
+                if (ss >= 0) tl[2 * na + 2 * ss] += 1.0;
                 medium = to;
                 spawn_offset(pos, o_ray, th, Nf, -1.0);
                 continue;
             }
             if (!(u[3] < sp[4])) { fate = ORC_SURF_ABS; detail = sid; break; }
+            if (ss >= 0) tl[2 * na + 2 * ss + 1] += 1.0;
             double w[4];
             draw4(seed, pid, step, 1, w);
             reflect_specular = w[3] < sp[5];
@@ -766,6 +830,10 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
     if (fate == ORC_BULK_ABS) ty->fates[N_FIXED + detail] += 1;
     if (fate == ORC_SURF_ABS) ty->fates[N_FIXED + M + detail] += 1;
     if (fate == ORC_DETECTED || fate == ORC_QE_FAIL) ty->lce[detail] += 1;
+    if (fate == ORC_DETECTED && ty->adj) {
+        const int K = 2 * s->n_amat + 2 * s->n_asurf;
+        for (int k = 0; k < K; ++k) ty->adj[(uint64_t)detail * K + k] += tl[k];
+    }
     if (fate == ORC_DETECTED) {
         ty->det[detail] += 1;
         double b = floor(time / tbin);
@@ -818,6 +886,8 @@ int orc_propagate(const orc_scene* s, const orc_source* src, uint64_t n, uint64_
         j->ty.det = (uint64_t*)calloc(P, 8);
         j->ty.hist = (uint64_t*)calloc(P * (n_tbins + 1ull), 8);
         j->ty.fates = (uint64_t*)calloc(NF, 8);
+        const uint64_t K = 2ull * s->n_amat + 2ull * s->n_asurf;
+        j->ty.adj = (out->adjoint && K) ? (double*)calloc(P * K, 8) : NULL;
         pthread_create(&th[t], NULL, worker, j);
     }
     for (int t = 0; t < n_threads; ++t) {
@@ -831,6 +901,11 @@ int orc_propagate(const orc_scene* s, const orc_source* src, uint64_t n, uint64_
             for (uint64_t c = 0; c < P * (n_tbins + 1ull); ++c) out->hist[c] += j->ty.hist[c];
         if (out->fates)
             for (uint64_t c = 0; c < NF; ++c) out->fates[c] += j->ty.fates[c];
+        if (j->ty.adj) {
+            const uint64_t K = 2ull * s->n_amat + 2ull * s->n_asurf;
+            for (uint64_t c = 0; c < P * K; ++c) out->adjoint[c] += j->ty.adj[c];
+            free(j->ty.adj);
+        }
         free(j->ty.lce); free(j->ty.det); free(j->ty.hist); free(j->ty.fates);
     }
     free(jobs);

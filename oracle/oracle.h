@@ -79,11 +79,25 @@ typedef struct {
     int32_t* ph_detail;   /* optional [n]: channel / material / surface / triangle */
     uint32_t* ph_steps;   /* optional [n] */
     float* ph_time;       /* optional [n]: time at the end (ns) */
-    double* adjoint;      /* optional [P*12]: per-channel sums of detected-photon tallies */
+    double* adjoint;      /* optional [P*K]: per-channel sums of the detected photons' tallies
+                             (K = 2*n_mat + 2*n_surf of orc_set_adjoint) */
 } orc_results;
 
 int orc_propagate(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
                   uint32_t max_steps, double tbin_ns, uint32_t n_tbins, orc_results* out, int n_threads);
+
+/* Score-function adjoint: per photon, tally the path length and the Rayleigh
+ * count in each tracked material and, for each tracked surface, the number
+ * of reflections (REFLECTOR) or of transmissions and wire reflections
+ * (ELECTRODE_T); sums over detected photons per channel go to
+ * orc_results.adjoint.  Tally k layout: material i -> 2i (length), 2i+1
+ * (Rayleigh count); surface j -> 2n_mat+2j (reflections / transmissions),
+ * 2n_mat+2j+1 (wire reflections). */
+int orc_set_adjoint(orc_scene* s, const int* mats, int n_mats, const int* surfs, int n_surfs);
+/* Jacobian d E[detected hits of channel c] / d theta_q from the tally sums
+ * [P*K]: theta = (L_abs, L_ray) of each tracked material, then R (REFLECTOR)
+ * or T (ELECTRODE_T) of each tracked surface; J [P * (2 n_mat + n_surf)]. */
+void orc_jacobian(const orc_scene* s, const double* sums, double* J);
 
 /* pieces exposed for the closed-form checks */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -783,3 +783,21 @@ def electrode_box(transparency=0.9, r_wire=0.3, wire_spec_frac=0.0, half=500.0, 
     src = Source(SRC_POINT, 0, center=(0.0, 0.0, 0.5 * (z_bot + z_el)))
     return Detector("electrode_box", verts, tris, mi, mo, sf, ch, mats, surfs, np.array([0, 1], np.int32),
                     np.array([[0, 0, z_bot], [0, 0, z_top]], np.float32), src, dict())
+
+
+def reflector_box(reflectivity=0.8, spec_frac=1.0, half=500.0, z_bot=-100.0, z_top=100.0, mat_n=1.69):
+    """LXe box with a reflecting floor (surface 1), a photocathode ceiling with
+    QE 1 (channel 0) and black side walls; for the reflectivity checks."""
+    mats = [Material("LXe", mat_n), Material("opaque", 1.0)]
+    surfs = [Surface("black", ABSORBER), Surface("floor", REFLECTOR, reflectivity, spec_frac),
+             Surface("photocathode", PHOTOCATHODE, qe=1.0)]
+    sq = np.array([[-half, -half], [half, -half], [half, half], [-half, half]], np.float64)
+    b = _Builder()
+    b.add(_fan(sq, z_bot, (0, 0)), (0, 0, -1), 0, 1, 1)
+    b.add(_fan(sq, z_top, (0, 0)), (0, 0, 1), 0, 1, 2, 0)
+    _wall(b, sq, z_bot, z_top, 0, 0)
+    verts, tris, mi, mo, sf, ch = b.finish()
+    mo[mo == OPAQUE] = 1
+    src = Source(SRC_POINT, 0, center=(0.0, 0.0, 0.0))
+    return Detector("reflector_box", verts, tris, mi, mo, sf, ch, mats, surfs, np.array([1], np.int32),
+                    np.array([[0, 0, z_top]], np.float32), src, dict())
