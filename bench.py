@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--photons", type=float, default=1e8, help="photons per rank per step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+adjoint cost measurement")
     return ap.parse_args()
 
 
@@ -132,6 +133,46 @@ def cpu_baseline(det, target_s):
     return {"value": n / dt, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
             "sample": f"{n} photons of the same workload (seed 12345), {dt:.1f} s wall on {res['threads']} threads; "
                       f"scene build excluded"}, res, n
+
+
+def adjoint_cost(args, n=10_000_000, reps=3):
+    """Forward + adjoint against the plain forward on the 50 cm TPC with 61 +
+    61 PMTs and thin-disk electrodes, 1e7 photons, 7 parameters: the time of
+    the propagation with per-photon tallies (and the Jacobian kernel) over the
+    time of the plain propagation, same photons."""
+    import torch
+    from paper_2203_14354_gb300 import geometry, Tracker
+    det = geometry.scaled_tpc()
+    trk = Tracker(det)
+    trk.set_adjoint([geometry.LXE], [0, 1, 4, 5, 6])
+    out = trk.alloc_results(1000)
+    out["adjoint"] = torch.zeros((trk.n_channels, trk.n_tallies), dtype=torch.float64, device=trk.device)
+
+    def run(adj):
+        for v in out.values():
+            v.zero_()
+        trk.propagate(n, seed=5, out=out, adjoint=adj, sync=False)
+        if adj:
+            trk.jacobian(out["adjoint"])
+
+    for adj in (False, True):
+        run(adj)
+    trk.sync()
+    times = {}
+    for adj in (False, True):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run(adj)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        times[adj] = statistics.median(ts)
+    trk.sync()
+    return {"workload": "50 cm dual-phase TPC, 61+61 PMTs, thin-disk gate/anode/cathode, 1e7 photons, 7 parameters",
+            "fwd_ms": times[False], "fwd_adjoint_ms": times[True], "ratio": times[True] / times[False],
+            "fwd_photons_per_s": n / (times[False] / 1e3)}
 
 
 def run_reference(args, rank, world):
@@ -269,6 +310,8 @@ def main():
     from paper_2203_14354_gb300 import _capi
     h2d = ctypes.sizeof(_capi.lxo_source) + ctypes.sizeof(_capi.lxo_run_params)
 
+    adjoint = adjoint_cost(args) if (rank == 0 and not args.no_adjoint) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_baseline(det, args.cpu_seconds)
@@ -301,6 +344,8 @@ def main():
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

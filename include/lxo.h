@@ -138,7 +138,12 @@ typedef struct {
 } lxo_run_params;
 
 /* run flags */
-#define LXO_FLAG_STATS 1u  /* count traversal work into lxo_results.stats (a separate kernel build) */
+#define LXO_FLAG_STATS 1u    /* count traversal work into lxo_results.stats (a separate kernel build) */
+#define LXO_FLAG_ADJOINT 2u  /* accumulate the adjoint tallies of detected photons into lxo_results.adjoint */
+
+/* adjoint limits */
+#define LXO_ADJ_MAX_MATERIALS 4
+#define LXO_ADJ_MAX_SURFACES 8
 
 /* fate codes (per photon) */
 enum {
@@ -164,6 +169,8 @@ typedef struct {
     int32_t* ph_detail;          /* optional device [n]: channel / material / surface / triangle */
     uint32_t* ph_steps;          /* optional device [n] */
     float* ph_time;              /* optional device [n]: time at the end, ns */
+    double* adjoint;             /* device [P*K] with LXO_FLAG_ADJOINT: per channel, sums over detected
+                                    photons of their tallies (layout of lxo_set_adjoint) */
     unsigned long long* stats;   /* device [32] with LXO_FLAG_STATS (accumulated): [0..3] photon steps,
                                     BVH nodes visited, leaves visited, triangles tested (lane counts);
                                     [4..6] warp iterations of the node loop, of the leaf loop and of
@@ -239,6 +246,32 @@ lxo_status lxo_propagate(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64
  * copies the tallies back and ADDS them to the host arrays.  Synchronous. */
 lxo_status lxo_propagate_host(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
                               const lxo_run_params* params, const lxo_results* host_out, void* stream);
+
+/* Adjoint (an extension of the paper's method: it has no gradients; the
+ * quantities are its Table 2 parameters and the Sec. 2.1 electrode model).
+ * The gradient of expected detected hits per channel with respect to
+ *   theta = (L_abs, L_ray) of each material in `mats`, then R (REFLECTOR) or
+ *           T (ELECTRODE_T) of each surface in `surfs`
+ * is the score-function estimator: each photon tallies, in FP32,
+ *   K = 2*n_mats + 2*n_surfs numbers -- for material i: path length (2i) and
+ *   Rayleigh scatters (2i+1); for surface j: reflections or transmissions
+ *   (2n_mats+2j) and wire reflections (2n_mats+2j+1) --
+ * and on detection adds them (FP64) to lxo_results.adjoint[channel*K + k].
+ * A detected path's log-probability has the derivatives
+ *   d/dL_abs = l/L_abs^2, d/dL_ray = l/L_ray^2 - N/L_ray, d/dR = n/R,
+ *   d/dT = n_T/T - n_W/(1-T),
+ * so lxo_adjoint_jacobian turns the sums into J[channel][q] = dE[hits]/dtheta_q.
+ * Host arrays; n_mats <= LXO_ADJ_MAX_MATERIALS, n_surfs <= LXO_ADJ_MAX_SURFACES;
+ * surfaces must be REFLECTOR or ELECTRODE_T. */
+lxo_status lxo_set_adjoint(lxo_ctx* ctx, const int32_t* mats, uint32_t n_mats, const int32_t* surfs,
+                           uint32_t n_surfs);
+
+/* J [P*Q] (device, row = channel, Q = 2*n_mats + n_surfs) from the tally
+ * sums [P*K] (device) at the current material / surface values; if g (device
+ * [P]) and grad (device [Q]) are not NULL, also grad = J^T g (the
+ * vector-Jacobian product of a backward pass).  Asynchronous on `stream`. */
+lxo_status lxo_adjoint_jacobian(lxo_ctx* ctx, const double* tally_sums, double* J, const double* g, double* grad,
+                                void* stream);
 
 /* Waits for `stream` and reports a device-side fault recorded since the last
  * lxo_sync (then clears it). */

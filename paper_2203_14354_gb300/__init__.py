@@ -8,11 +8,11 @@ dual-phase TPC, arXiv:2203.14354).
 """
 from . import geometry  # noqa: F401
 
-__all__ = ["geometry", "Tracker"]
+__all__ = ["geometry", "Tracker", "LightCollection"]
 
 
 def __getattr__(name):
-    if name == "Tracker":
-        from .tracker import Tracker
-        return Tracker
+    if name in ("Tracker", "LightCollection"):
+        from . import tracker
+        return getattr(tracker, name)
     raise AttributeError(name)

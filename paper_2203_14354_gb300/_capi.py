@@ -16,6 +16,7 @@ LXO_MAX_SURFACES = 48
 LXO_SURF_NONE = 0xFFFF
 LXO_NO_HIT = 0xFFFFFFFF
 LXO_FLAG_STATS = 1
+LXO_FLAG_ADJOINT = 2
 LXO_STATIC_SCRATCH_BYTES = 8 << 20
 FATE_NAMES = ["detected", "qe_fail", "bulk_abs", "surf_abs", "escaped", "truncated", "geom_err"]
 
@@ -48,7 +49,7 @@ class lxo_run_params(C.Structure):
 class lxo_results(C.Structure):
     _fields_ = [("lce", C.c_void_p), ("det", C.c_void_p), ("hist", C.c_void_p), ("fates", C.c_void_p),
                 ("ph_fate", C.c_void_p), ("ph_detail", C.c_void_p), ("ph_steps", C.c_void_p),
-                ("ph_time", C.c_void_p), ("stats", C.c_void_p)]
+                ("ph_time", C.c_void_p), ("adjoint", C.c_void_p), ("stats", C.c_void_p)]
 
 
 class lxo_bvh_info(C.Structure):
@@ -79,6 +80,8 @@ _SIGNATURES = {
     "lxo_propagate_host": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,
                                      C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
     "lxo_sync": (C.c_int, [vp, vp]),
+    "lxo_set_adjoint": (C.c_int, [vp, vp, C.c_uint32, vp, C.c_uint32]),
+    "lxo_adjoint_jacobian": (C.c_int, [vp, vp, vp, vp, vp, vp]),
     "lxo_propagate_host_static": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,
                                             C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
 }

@@ -29,6 +29,7 @@ struct lxo_ctx {
     std::vector<lxo_material> mats;
     std::vector<lxo_surface> surfs;
     std::vector<lxo_pmt> pmts;
+    std::vector<int32_t> adj_mats, adj_surfs;
     // device
     float4* d_nodes = nullptr;
     float4* d_tris = nullptr;
@@ -182,6 +183,22 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
     }
     p->queue = c->d_queue;
     p->err = c->d_err;
+    for (int m = 0; m < LXO_MAX_MATERIALS; ++m) p->adj_mat_slot[m] = -1;
+    for (int q = 0; q < LXO_MAX_SURFACES; ++q) p->adj_surf_slot[q] = -1;
+    p->adj_k = 0;
+    p->adj_n_mats = (int)c->adj_mats.size();
+    if (rp && (rp->flags & LXO_FLAG_ADJOINT)) {
+        for (size_t i = 0; i < c->adj_mats.size(); ++i) {
+            if (c->adj_mats[i] >= M) return fail(c, LXO_ERR_ARG, "adjoint material %d >= %d", c->adj_mats[i], M);
+            p->adj_mat_slot[c->adj_mats[i]] = (signed char)i;
+        }
+        for (size_t j = 0; j < c->adj_surfs.size(); ++j) {
+            if (c->adj_surfs[j] >= S) return fail(c, LXO_ERR_ARG, "adjoint surface %d >= %d", c->adj_surfs[j], S);
+            p->adj_surf_slot[c->adj_surfs[j]] = (signed char)j;
+        }
+        p->adj_k = 2 * (int)(c->adj_mats.size() + c->adj_surfs.size());
+        if (p->adj_k == 0) return fail(c, LXO_ERR_ARG, "LXO_FLAG_ADJOINT without tracked parameters");
+    }
     return LXO_OK;
 }
 
@@ -425,6 +442,8 @@ lxo_status lxo_propagate(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t
         return fail(c, LXO_ERR_ARG, "propagate: lce, det, hist and fates buffers are required");
     if ((rp->flags & LXO_FLAG_STATS) && !out->stats)
         return fail(c, LXO_ERR_ARG, "propagate: LXO_FLAG_STATS needs the stats buffer");
+    if ((rp->flags & LXO_FLAG_ADJOINT) && !out->adjoint)
+        return fail(c, LXO_ERR_ARG, "propagate: LXO_FLAG_ADJOINT needs the adjoint buffer");
     if (n == 0) return LXO_OK;
     lxo::PropParams p;
     s = fill_params(c, src, n, base, rp, &p);
@@ -446,9 +465,11 @@ lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uin
     if (!rp) return fail(c, LXO_ERR_ARG, "propagate_host: run params are NULL");
     if (!host_out || !host_out->lce || !host_out->det || !host_out->hist || !host_out->fates)
         return fail(c, LXO_ERR_ARG, "propagate_host: lce, det, hist and fates buffers are required");
-    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->stats)
-        return fail(c, LXO_ERR_ARG, "propagate_host: per-photon outputs and stats are device-only");
-    if (rp->flags & LXO_FLAG_STATS) return fail(c, LXO_ERR_ARG, "propagate_host: LXO_FLAG_STATS not supported");
+    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->stats ||
+        host_out->adjoint)
+        return fail(c, LXO_ERR_ARG, "propagate_host: per-photon outputs, stats and adjoint are device-only");
+    if (rp->flags & (LXO_FLAG_STATS | LXO_FLAG_ADJOINT))
+        return fail(c, LXO_ERR_ARG, "propagate_host: LXO_FLAG_STATS / LXO_FLAG_ADJOINT not supported");
     const size_t P = c->pmts.size(), B = (size_t)rp->n_tbins + 1;
     const size_t NF = LXO_FATES_FIXED + c->mats.size() + c->surfs.size();
     const size_t bytes = 8 * NF + 4 * (2 * P + P * B);
@@ -481,6 +502,61 @@ lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uin
         host_out->det[i] += hu[P + i];
     }
     for (size_t i = 0; i < P * B; ++i) host_out->hist[i] += hu[2 * P + i];
+    return LXO_OK;
+}
+
+lxo_status lxo_set_adjoint(lxo_ctx* c, const int32_t* mats, uint32_t n_mats, const int32_t* surfs, uint32_t n_surfs)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (n_mats > LXO_ADJ_MAX_MATERIALS || n_surfs > LXO_ADJ_MAX_SURFACES || (n_mats && !mats) || (n_surfs && !surfs))
+        return fail(c, LXO_ERR_ARG, "set_adjoint: at most %d materials and %d surfaces", LXO_ADJ_MAX_MATERIALS,
+                    LXO_ADJ_MAX_SURFACES);
+    for (uint32_t i = 0; i < n_mats; ++i) {
+        if (mats[i] < 0 || mats[i] >= LXO_MAX_MATERIALS) return fail(c, LXO_ERR_ARG, "set_adjoint: material %d", mats[i]);
+        for (uint32_t k = 0; k < i; ++k)
+            if (mats[k] == mats[i]) return fail(c, LXO_ERR_ARG, "set_adjoint: material %d twice", mats[i]);
+    }
+    for (uint32_t j = 0; j < n_surfs; ++j) {
+        if (surfs[j] < 0 || surfs[j] >= (int32_t)c->surfs.size())
+            return fail(c, LXO_ERR_ARG, "set_adjoint: surface %d not in the surface table", surfs[j]);
+        const int t = c->surfs[surfs[j]].type;
+        if (t != LXO_SURF_REFLECTOR && t != LXO_SURF_ELECTRODE_T)
+            return fail(c, LXO_ERR_ARG, "set_adjoint: surface %d is neither a reflector nor an electrode", surfs[j]);
+        for (uint32_t k = 0; k < j; ++k)
+            if (surfs[k] == surfs[j]) return fail(c, LXO_ERR_ARG, "set_adjoint: surface %d twice", surfs[j]);
+    }
+    c->adj_mats.assign(mats, mats + n_mats);
+    c->adj_surfs.assign(surfs, surfs + n_surfs);
+    return LXO_OK;
+}
+
+lxo_status lxo_adjoint_jacobian(lxo_ctx* c, const double* sums, double* J, const double* g, double* grad, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!sums || !J || (!g) != (!grad)) return fail(c, LXO_ERR_ARG, "adjoint_jacobian: NULL array");
+    const int nm = (int)c->adj_mats.size(), ns = (int)c->adj_surfs.size();
+    const int K = 2 * (nm + ns), Q = 2 * nm + ns, P = (int)c->pmts.size();
+    if (K == 0 || P == 0) return fail(c, LXO_ERR_STATE, "adjoint_jacobian: no tracked parameters or no PMTs");
+    lxo::AdjCoef coef[2 * LXO_ADJ_MAX_MATERIALS + LXO_ADJ_MAX_SURFACES];
+    for (int i = 0; i < nm; ++i) {
+        const lxo_material& m = c->mats[c->adj_mats[i]];
+        const double La = (m.abs_len_mm > 0.0f && std::isfinite(m.abs_len_mm)) ? m.abs_len_mm : INFINITY;
+        const double Lr = (m.rayleigh_len_mm > 0.0f && std::isfinite(m.rayleigh_len_mm)) ? m.rayleigh_len_mm : INFINITY;
+        coef[2 * i] = lxo::AdjCoef{2 * i, 2 * i, std::isinf(La) ? 0.0 : 1.0 / (La * La), 0.0};
+        coef[2 * i + 1] = lxo::AdjCoef{2 * i, 2 * i + 1, std::isinf(Lr) ? 0.0 : 1.0 / (Lr * Lr),
+                                       std::isinf(Lr) ? 0.0 : -1.0 / Lr};
+    }
+    for (int j = 0; j < ns; ++j) {
+        const lxo_surface& sf = c->surfs[c->adj_surfs[j]];
+        const int ia = 2 * nm + 2 * j;
+        if (sf.type == LXO_SURF_REFLECTOR)
+            coef[2 * nm + j] = lxo::AdjCoef{ia, ia + 1, sf.reflectivity > 0.0f ? 1.0 / sf.reflectivity : 0.0, 0.0};
+        else
+            coef[2 * nm + j] = lxo::AdjCoef{ia, ia + 1, sf.transparency > 0.0f ? 1.0 / sf.transparency : 0.0,
+                                            sf.transparency < 1.0f ? -1.0 / (1.0 - sf.transparency) : 0.0};
+    }
+    DeviceGuard gd(c->device);
+    CK(lxo::launch_adjoint_jacobian(coef, Q, K, P, sums, J, g, grad, (cudaStream_t)stream), "adjoint_jacobian");
     return LXO_OK;
 }
 
@@ -537,8 +613,8 @@ extern "C" lxo_status lxo_propagate_host_static(lxo_ctx* c, const lxo_source* sr
     if (!host_out || !host_out->lce || !host_out->det || !host_out->hist || !host_out->fates)
         return static_fail(c, LXO_ERR_ARG, "lce, det, hist, fates host buffers required");
     if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->stats ||
-        (rp->flags & LXO_FLAG_STATS))
-        return static_fail(c, LXO_ERR_ARG, "per-photon outputs and stats unsupported");
+        host_out->adjoint || (rp->flags & (LXO_FLAG_STATS | LXO_FLAG_ADJOINT)))
+        return static_fail(c, LXO_ERR_ARG, "per-photon outputs, stats and adjoint unsupported");
     lxo_status s = validate(c);
     if (s) return s;
     const uint64_t P = c->pmts.size(), B = (uint64_t)rp->n_tbins + 1;

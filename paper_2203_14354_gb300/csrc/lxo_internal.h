@@ -123,6 +123,10 @@ struct PropParams {
     uint32_t max_steps, n_tbins, flags;
     float tbin;
     lxo_results out;
+    int adj_k;                                   // tallies per photon (0 = no adjoint)
+    signed char adj_mat_slot[LXO_MAX_MATERIALS]; // tracked material -> index, -1 if not
+    signed char adj_surf_slot[LXO_MAX_SURFACES]; // tracked surface -> index, -1 if not
+    int adj_n_mats;
     unsigned long long* queue;   // scratch: work-queue head
     int* err;                    // scratch: device error word
 };
@@ -132,5 +136,12 @@ cudaError_t launch_trace(const Scene& sc, const float* org, const float* dir, co
                          const float* tmax, uint32_t n, uint32_t* hit, float* t, int* err, cudaStream_t st);
 cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, cudaStream_t st);
 cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st);
+
+struct AdjCoef {   // per parameter q: J[c][q] = a * sums[c][ia] + b * sums[c][ib]
+    int ia, ib;
+    double a, b;
+};
+cudaError_t launch_adjoint_jacobian(const AdjCoef* coef_host, int Q, int K, int P, const double* sums, double* J,
+                                    const double* g, double* grad, cudaStream_t st);
 
 }  // namespace lxo

@@ -27,6 +27,7 @@
 namespace lxo {
 
 #define FULL_MASK 0xFFFFFFFFu
+constexpr int kPropThreadsK = 256;  // threads per CTA of the propagation kernel (stride of the adjoint tallies)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
@@ -637,11 +638,17 @@ __device__ __forceinline__ void step_histogram(const PropParams& p, const Photon
 // Second half of a step: the interaction at the closest hit or in the bulk.
 // Returns -1 if the photon lives on, else its fate code (detail set to
 // channel / material / surface / triangle).
-__device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, const Hit& h, int& detail)
+// Adjoint tallies of one lane live in shared memory, tally k at tl[k * kPropThreads].
+constexpr int kAdjMaxK = 2 * (LXO_ADJ_MAX_MATERIALS + LXO_ADJ_MAX_SURFACES);
+
+template <bool kAdjoint>
+__device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, const Hit& h, int& detail,
+                           float* tl)
 {
     const float d_abs = sd.d_abs, d_ray = sd.d_ray, d_int = fminf(d_abs, d_ray);
     const U4 u = U4{0.0f, 0.0f, sd.u2, sd.u3};
     const DevMaterial& mt = p.mat[ph.medium];
+    const int ms = kAdjoint ? p.adj_mat_slot[ph.medium] : -1;
     if (h.id == LXO_NO_HIT) {
         if (isinf(d_int)) {
             detail = -1;
@@ -649,10 +656,12 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
         }
         ph.pos = ph.pos + d_int * ph.dir;
         ph.time += d_int * mt.n_over_c;
+        if (kAdjoint && ms >= 0) tl[(2 * ms) * kPropThreadsK] += d_int;
         if (d_abs <= d_ray) {
             detail = ph.medium;
             return LXO_FATE_BULK_ABS;
         }
+        if (kAdjoint && ms >= 0) tl[(2 * ms + 1) * kPropThreadsK] += 1.0f;
         rayleigh(ph, p.seed);
         ph.last = LXO_NO_HIT;
         return -1;
@@ -660,6 +669,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
     const float3 o_ray = ph.pos;
     ph.pos = ph.pos + h.t * ph.dir;
     ph.time += h.t * mt.n_over_c;
+    if (kAdjoint && ms >= 0) tl[(2 * ms) * kPropThreadsK] += h.t;
     // geometric normal and attributes of the triangle hit (record in leaf order)
     const float4* tr = p.sc.tris + 3 * (size_t)h.rec;
     const float4 va = __ldg(tr + 0), vb = __ldg(tr + 1), vc = __ldg(tr + 2);
@@ -699,11 +709,14 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
         return (u.u2 < sf.qe) ? LXO_FATE_DETECTED : LXO_FATE_QE_FAIL;
     }
     bool specular;
+    const int ss = kAdjoint ? p.adj_surf_slot[sid] : -1;
+    const int base_k = 2 * p.adj_n_mats + 2 * ss;
     if (sf.type == LXO_SURF_REFLECTOR) {
         if (!(u.u2 < sf.R)) {
             detail = (int)sid;
             return LXO_FATE_SURF_ABS;
         }
+        if (kAdjoint && ss >= 0) tl[base_k * kPropThreadsK] += 1.0f;
         specular = u.u3 < sf.spec;
     } else if (sf.type == LXO_SURF_ELECTRODE_T) {
         if (u.u2 < sf.T) {
@@ -711,6 +724,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
                 detail = (int)h.id;
                 return LXO_FATE_GEOM_ERR;
             }
+            if (kAdjoint && ss >= 0) tl[base_k * kPropThreadsK] += 1.0f;
             ph.medium = to;
             spawn_offset(ph, o_ray, h.t, Nf, -1.0f);
             return -1;
@@ -719,6 +733,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
             detail = (int)sid;
             return LXO_FATE_SURF_ABS;
         }
+        if (kAdjoint && ss >= 0) tl[(base_k + 1) * kPropThreadsK] += 1.0f;
         specular = draw4(p.seed, ph.pid, ph.step, 1).u3 < sf.wspec;
     } else {
         detail = (int)h.id;
@@ -733,8 +748,8 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
 }
 
 // one whole interaction (draw, closest hit, interaction)
-template <bool kStats>
-__device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counters& cnt)
+template <bool kStats, bool kAdjoint>
+__device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counters& cnt, float* tl)
 {
     const StepDraw sd = begin_step(p, ph);
     const long long c0 = kStats ? clock64() : 0;
@@ -744,13 +759,13 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
         cnt.trav_cycles += (unsigned long long)(clock64() - c0);
         step_histogram<kStats>(p, ph, cnt.nodes - n0, cnt.leaves - l0);
     }
-    return finish_step(p, ph, sd, h, detail);
+    return finish_step<kAdjoint>(p, ph, sd, h, detail, tl);
 }
 
 // ---------------------------------------------------------------------------
 // persistent propagation kernel
 // ---------------------------------------------------------------------------
-constexpr int kPropThreads = 256;
+constexpr int kPropThreads = kPropThreadsK;
 constexpr uint32_t kChunk = 64;
 // tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
 // idle; 5 CTAs of 256 threads per SM (51 registers) hide more L1/L2 latency
@@ -764,9 +779,13 @@ constexpr uint32_t kChunk = 64;
 
 // Tally of one photon's fate: shared-memory fate counters, global per-channel
 // counts and arrival-time histogram, optional per-photon record.
+template <bool kAdjoint>
 __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s_f, const Photon& ph, int fate,
-                                      int detail)
+                                      int detail, const float* tl)
 {
+    if (kAdjoint && fate == LXO_FATE_DETECTED)
+        for (int k = 0; k < p.adj_k; ++k)
+            atomicAdd(&p.out.adjoint[(size_t)detail * p.adj_k + k], (double)tl[k * kPropThreads]);
     atomicAdd(&s_f[fate], 1ull);
     atomicAdd(&s_f[7], (unsigned long long)ph.step);
     if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
@@ -793,13 +812,15 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
 // from a warp-local chunk (ballot + prefix popcount), chunks of kChunk ids
 // coming from the global work-queue head.  Source sampling and tallies thus
 // run on many lanes at once instead of one lane per iteration.
-template <bool kStats>
+template <bool kStats, bool kAdjoint>
 __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(const __grid_constant__ PropParams p)
 {
     Counters cnt{};
     uint32_t my_steps = 0, outer_iters = 0;
     unsigned long long loop_cycles = 0;
     __shared__ unsigned long long s_f[kMaxFates];
+    __shared__ float s_tl[kAdjoint ? kAdjMaxK * kPropThreads : 1];
+    float* tl = kAdjoint ? &s_tl[threadIdx.x] : nullptr;
     for (int i = threadIdx.x; i < p.n_fates; i += blockDim.x) s_f[i] = 0ull;
     __syncthreads();
 
@@ -816,7 +837,7 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
         const int idle = __popc(need);
         if (idle >= LXO_REFILL_MIN || idle == 32) {
             if (pending) {
-                tally(p, s_f, ph, fate, detail);
+                tally<kAdjoint>(p, s_f, ph, fate, detail, tl);
                 pending = false;
             }
             while (need && !exhausted) {
@@ -836,6 +857,8 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
                 const uint32_t rank = __popc(need & lt_mask);
                 if (((need >> lane) & 1u) && rank < take) {
                     ph = make_photon(p, chunk_next + rank);
+                    if (kAdjoint)
+                        for (int k = 0; k < p.adj_k; ++k) tl[k * kPropThreads] = 0.0f;
                     alive = true;
                 }
                 chunk_next += take;
@@ -846,7 +869,7 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
         if (kStats && lane == 0) outer_iters++;
         const long long c0 = kStats ? clock64() : 0;
         if (alive) {
-            fate = photon_step<kStats>(p, ph, detail, cnt);
+            fate = photon_step<kStats, kAdjoint>(p, ph, detail, cnt, tl);
             ph.step++;
             if (kStats) my_steps++;
             if (fate < 0 && ph.step >= p.max_steps) fate = LXO_FATE_TRUNCATED;
@@ -901,13 +924,62 @@ cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
     const bool stats = (p.flags & LXO_FLAG_STATS) != 0;
-    auto kern = stats ? k_propagate<true> : k_propagate<false>;
+    const bool adj = (p.flags & LXO_FLAG_ADJOINT) != 0;
+    auto kern = stats ? (adj ? k_propagate<true, true> : k_propagate<true, false>)
+                      : (adj ? k_propagate<false, true> : k_propagate<false, false>);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPropThreads, 0);
     if (e != cudaSuccess) return e;
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
     const uint64_t need = (p.n + kPropThreads - 1) / kPropThreads;
     if (need < blocks) blocks = need;
     kern<<<(unsigned)blocks, kPropThreads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// adjoint backward: J[c][q] = a_q * sums[c][ia_q] + b_q * sums[c][ib_q];
+// optional grad[q] = sum_c g[c] J[c][q]
+// ---------------------------------------------------------------------------
+struct AdjCoefs {
+    AdjCoef c[2 * LXO_ADJ_MAX_MATERIALS + LXO_ADJ_MAX_SURFACES];
+};
+
+__global__ void k_adjoint_jacobian(const AdjCoefs co, int Q, int K, int P, const double* __restrict__ sums,
+                                   double* __restrict__ J)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * Q) return;
+    const int ch = i / Q, q = i % Q;
+    const AdjCoef& c = co.c[q];
+    J[i] = c.a * sums[(size_t)ch * K + c.ia] + c.b * sums[(size_t)ch * K + c.ib];
+}
+
+__global__ void k_adjoint_vjp(int Q, int P, const double* __restrict__ J, const double* __restrict__ g,
+                              double* __restrict__ grad)
+{
+    __shared__ double red[256];
+    const int q = blockIdx.x;
+    double acc = 0.0;
+    for (int ch = threadIdx.x; ch < P; ch += blockDim.x) acc += g[ch] * J[(size_t)ch * Q + q];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) grad[q] = red[0];
+}
+
+cudaError_t launch_adjoint_jacobian(const AdjCoef* coef_host, int Q, int K, int P, const double* sums, double* J,
+                                    const double* g, double* grad, cudaStream_t st)
+{
+    AdjCoefs co;
+    for (int q = 0; q < Q; ++q) co.c[q] = coef_host[q];
+    const int n = P * Q, threads = 256;
+    k_adjoint_jacobian<<<(n + threads - 1) / threads, threads, 0, st>>>(co, Q, K, P, sums, J);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !g) return e;
+    k_adjoint_vjp<<<Q, 256, 0, st>>>(Q, P, J, g, grad);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,63 @@ class Tracker:
     def n_fates(self):
         return A.LXO_FATES_FIXED + self.n_materials + self.n_surfaces
 
+    # -- adjoint --------------------------------------------------------------
+    def set_adjoint(self, mats=(), surfs=()):
+        """Track theta = (L_abs, L_ray) of each material in `mats`, then R
+        (reflector) or T (electrode) of each surface in `surfs`."""
+        m = (C.c_int32 * max(1, len(mats)))(*mats)
+        sf = (C.c_int32 * max(1, len(surfs)))(*surfs)
+        self._check(self._L.lxo_set_adjoint(self._ctx, m, len(mats), sf, len(surfs)))
+        self.adj_mats, self.adj_surfs = list(mats), list(surfs)
+
+    @property
+    def n_tallies(self):
+        return 2 * (len(self.adj_mats) + len(self.adj_surfs))
+
+    @property
+    def n_params(self):
+        return 2 * len(self.adj_mats) + len(self.adj_surfs)
+
+    def theta(self):
+        """Current values of the tracked parameters (float64 tensor [Q])."""
+        v = []
+        for m in self.adj_mats:
+            v += [self.det.materials[m].abs_len_mm, self.det.materials[m].rayleigh_len_mm]
+        for q in self.adj_surfs:
+            sf = self.det.surfaces[q]
+            v.append(sf.reflectivity if sf.type == 1 else sf.transparency)
+        return torch.tensor(v, dtype=torch.float64)
+
+    def set_theta(self, theta):
+        """Writes the tracked parameters back into the material / surface tables."""
+        th = [float(x) for x in (theta.detach().cpu().tolist() if torch.is_tensor(theta) else theta)]
+        k = 0
+        for m in self.adj_mats:
+            self.det.materials[m].abs_len_mm, self.det.materials[m].rayleigh_len_mm = th[k], th[k + 1]
+            k += 2
+        for q in self.adj_surfs:
+            sf = self.det.surfaces[q]
+            if sf.type == 1:
+                sf.reflectivity = th[k]
+            else:
+                sf.transparency = th[k]
+            k += 1
+        self.set_materials(self.det.materials)
+        self.set_surfaces(self.det.surfaces)
+
+    def jacobian(self, sums, g=None, stream=None):
+        """J [P, Q] (and grad = J^T g [Q] if g is given) from adjoint tally sums
+        [P, K] at the current parameter values, computed on the device."""
+        sums = sums.contiguous()
+        J = torch.empty((self.n_channels, self.n_params), dtype=torch.float64, device=self.device)
+        grad = None
+        if g is not None:
+            g = g.to(device=self.device, dtype=torch.float64).contiguous()
+            grad = torch.empty(self.n_params, dtype=torch.float64, device=self.device)
+        self._check(self._L.lxo_adjoint_jacobian(self._ctx, _ptr(sums), _ptr(J), _ptr(g), _ptr(grad),
+                                                 _stream(stream)))
+        return J if g is None else (J, grad)
+
     # -- geometry query -----------------------------------------------------
     def trace_rays(self, org, dir, skip=None, tmax=None, stream=None):
         org = org.contiguous()
@@ -163,22 +220,28 @@ class Tracker:
             r.ph_steps, r.ph_time = out["steps"].data_ptr(), out["time"].data_ptr()
         if "stats" in out:
             r.stats = out["stats"].data_ptr()
+        if "adjoint" in out:
+            r.adjoint = out["adjoint"].data_ptr()
         return r
 
     def propagate(self, n, base=0, seed=0, source=None, explicit=None, max_steps=10000, n_tbins=1000, tbin_ns=1.0,
-                  per_photon=False, out=None, stream=None, sync=True, stats=False):
+                  per_photon=False, out=None, stream=None, sync=True, stats=False, adjoint=False):
         """Propagates photons base..base+n-1; returns (accumulates into) a dict
         of device tensors: lce, det [P], hist [P, n_tbins+1], fates [8+M+S]
         and, with per_photon, fate / detail / steps / time [n]; with stats,
-        stats [32] as documented for lxo_results.stats in include/lxo.h."""
+        stats [32] as documented for lxo_results.stats in include/lxo.h; with
+        adjoint, adjoint [P, K] (tally sums of detected photons)."""
         if out is None:
             out = self.alloc_results(n_tbins, n if per_photon else 0)
         if stats and "stats" not in out:
             out["stats"] = torch.zeros(32, dtype=torch.int64, device=self.device)
+        if adjoint and "adjoint" not in out:
+            out["adjoint"] = torch.zeros((self.n_channels, self.n_tallies), dtype=torch.float64, device=self.device)
         src = make_source(source or self.det.source, explicit)
         if explicit is not None and src.kind != SRC_EXPLICIT:
             raise ValueError("explicit arrays need an SRC_EXPLICIT source")
-        rp = A.lxo_run_params(seed, max_steps, n_tbins, tbin_ns, A.LXO_FLAG_STATS if stats else 0)
+        flags = (A.LXO_FLAG_STATS if stats else 0) | (A.LXO_FLAG_ADJOINT if adjoint else 0)
+        rp = A.lxo_run_params(seed, max_steps, n_tbins, tbin_ns, flags)
         res = self._results(out)
         st = _stream(stream)
         self._check(self._L.lxo_propagate(self._ctx, C.byref(src), n, base, C.byref(rp), C.byref(res), st))
@@ -203,3 +266,28 @@ class Tracker:
 
     def sync(self, stream=None):
         self._check(self._L.lxo_sync(self._ctx, _stream(stream)))
+
+
+class LightCollection(torch.autograd.Function):
+    """Expected detected hits per PMT as a differentiable function of the
+    tracked optical parameters theta (Tracker.set_adjoint): the forward pass
+    propagates `n` photons at theta with the adjoint tallies on; the backward
+    pass is the score-function gradient J^T g computed by the library's
+    adjoint kernels.  Returns float64 hits [P] (counts for n photons)."""
+
+    @staticmethod
+    def forward(ctx, theta, tracker, n, seed=0, source=None, base=0):
+        tracker.set_theta(theta)
+        out = tracker.propagate(n, base=base, seed=seed, source=source, adjoint=True)
+        ctx.tracker = tracker
+        ctx.theta = theta.detach().clone()
+        ctx.save_for_backward(out["adjoint"])
+        return out["det"].to(torch.float64)
+
+    @staticmethod
+    def backward(ctx, g):
+        (sums,) = ctx.saved_tensors
+        tr = ctx.tracker
+        tr.set_theta(ctx.theta)
+        _, grad = tr.jacobian(sums, g)
+        return grad.to(ctx.theta.device), None, None, None, None, None

@@ -1,0 +1,151 @@
+"""GPU adjoint (LXO_FLAG_ADJOINT, lxo_adjoint_jacobian) through the C ABI:
+closed-form derivatives, parity of the per-channel Jacobian with the oracle's
+independent adjoint, agreement with central finite differences under common
+random numbers, and the autograd Function's backward."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2203_14354_gb300 import geometry as g
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2203_14354_gb300 import tracker
+    return tracker
+
+
+def beam(n, z, up=True, seed=1, spread=10.0):
+    rng = np.random.default_rng(seed)
+    p = np.zeros((n, 3), np.float32)
+    p[:, 0] = rng.uniform(-spread, spread, n)
+    p[:, 1] = rng.uniform(-spread, spread, n)
+    p[:, 2] = z
+    d = np.zeros((n, 3), np.float32)
+    d[:, 2] = 1.0 if up else -1.0
+    a = rng.uniform(0, 2 * np.pi, n)
+    pol = np.stack([np.cos(a), np.sin(a), np.zeros(n)], 1).astype(np.float32)
+    return tuple(torch.from_numpy(x).cuda() for x in (p, d, pol))
+
+
+def test_gpu_adjoint_closed_forms(T):
+    lam, R, n = 100.0, 100.0, 400_000
+    trk = T.Tracker(g.icosphere(R, subdiv=5, abs_len_mm=lam))
+    trk.set_adjoint([0], [])
+    out = trk.propagate(n, adjoint=True)
+    J = trk.jacobian(out["adjoint"]).cpu().numpy()
+    want = n * R / lam ** 2 * math.exp(-R / lam)
+    sig = R / lam ** 2 * math.sqrt(n * math.exp(-R / lam) * (1 - math.exp(-R / lam)))
+    assert abs(J[0, 0] - want) < 4 * sig + 1e-3 * want
+    # electrode transparency: d top / dT = N
+    Tt, Rw = 0.9, 0.3
+    trk = T.Tracker(g.electrode_box(Tt, Rw))
+    trk.set_adjoint([], [2])
+    out = trk.propagate(n, source=g.Source(g.SRC_EXPLICIT, 0), explicit=beam(n, -50.0), adjoint=True)
+    J = trk.jacobian(out["adjoint"]).cpu().numpy()
+    assert abs(J[1, 0] - n) < 4 * math.sqrt(n * Tt * (1 - Tt)) / Tt
+    # mirror reflectivity: d top / dR = N
+    Rm = 0.8
+    trk = T.Tracker(g.reflector_box(Rm, 1.0))
+    trk.set_adjoint([], [1])
+    out = trk.propagate(n, source=g.Source(g.SRC_EXPLICIT, 0), explicit=beam(n, 0.0, up=False), adjoint=True)
+    J = trk.jacobian(out["adjoint"]).cpu().numpy()
+    assert abs(J[0, 0] - n) < 4 * math.sqrt(n * Rm * (1 - Rm)) / Rm
+
+
+def scaled_spec():
+    # theta = L_abs(LXe), L_ray(LXe), R(PTFE LXe), R(PTFE GXe), T(gate), T(anode), T(cathode)
+    return [g.LXE], [0, 1, 4, 5, 6]
+
+
+@pytest.fixture(scope="module")
+def scaled(T):
+    det = g.scaled_tpc()
+    trk = T.Tracker(det)
+    mats, surfs = scaled_spec()
+    trk.set_adjoint(mats, surfs)
+    orc = O.Oracle(det)
+    orc.set_adjoint(mats, surfs)
+    return det, trk, orc
+
+
+def test_gpu_adjoint_matches_oracle(scaled):
+    det, trk, orc = scaled
+    n = 200_000
+    out = trk.propagate(n, seed=3, adjoint=True)
+    sums_g = out["adjoint"].cpu().numpy()
+    J_g = trk.jacobian(out["adjoint"]).cpu().numpy()
+    ref = orc.propagate(n, seed=3, adjoint=True)
+    J_o = orc.jacobian(ref["adjoint"])
+    # the GPU Jacobian of the oracle's sums equals the oracle's Jacobian (same
+    # formula; the library holds the parameters in float32, hence 1e-6)
+    J_go = trk.jacobian(torch.from_numpy(ref["adjoint"]).cuda()).cpu().numpy()
+    np.testing.assert_allclose(J_go, J_o, rtol=1e-6, atol=1e-9)
+    # statistical parity of the tallies: totals and per array, per parameter
+    top = det.pmt_array == 1
+    for sel in (top, ~top, np.ones_like(top)):
+        a, b = J_g[sel].sum(0), J_o[sel].sum(0)
+        assert np.all(np.abs(a - b) <= 0.05 * np.abs(b) + 1e-6 * np.abs(J_o).max()), (a, b)
+    # the tallies themselves (path lengths, counts) agree per channel in sum
+    np.testing.assert_allclose(sums_g.sum(0), ref["adjoint"].sum(0), rtol=0.03)
+
+
+def test_gpu_adjoint_vs_central_fd_crn(scaled):
+    """Central finite differences with common random numbers (same seed and
+    photon ids at theta +- h): the total detected hits' derivative agrees
+    with the adjoint within their batch-means errors."""
+    det, trk, orc = scaled
+    theta0 = trk.theta()
+    n_b, B = 250_000, 8
+    rel = {0: 0.02, 1: 0.02, 2: 0.002, 3: 0.01, 4: 0.01, 5: 0.01, 6: 0.01}
+    adj = np.zeros((B, trk.n_params))
+    fd = np.zeros((B, trk.n_params))
+    trk.set_theta(theta0)
+    for b in range(B):
+        out = trk.propagate(n_b, base=b * n_b, seed=11, adjoint=True)
+        adj[b] = trk.jacobian(out["adjoint"]).sum(0).cpu().numpy()
+    for q, r in rel.items():
+        h = r * float(theta0[q])
+        for b in range(B):
+            tot = []
+            for sgn in (+1, -1):
+                th = theta0.clone()
+                th[q] += sgn * h
+                trk.set_theta(th)
+                out = trk.propagate(n_b, base=b * n_b, seed=11)
+                tot.append(float(out["det"].sum().item()))
+            fd[b, q] = (tot[0] - tot[1]) / (2 * h)
+    trk.set_theta(theta0)
+    a_m, a_s = adj.mean(0), adj.std(0, ddof=1) / math.sqrt(B)
+    f_m, f_s = fd.mean(0), fd.std(0, ddof=1) / math.sqrt(B)
+    z = np.abs(a_m - f_m) / np.sqrt(a_s ** 2 + f_s ** 2 + 1e-30)
+    assert np.all(z < 4.5), (a_m, f_m, a_s, f_s, z)
+    # where both estimates are sharp, they agree within 5 %
+    sharp = (a_s < 0.02 * np.abs(a_m)) & (f_s < 0.02 * np.abs(f_m))
+    assert np.all(np.abs(a_m[sharp] - f_m[sharp]) < 0.05 * np.abs(f_m[sharp]) + 4 * np.sqrt(a_s ** 2 + f_s ** 2)[sharp])
+
+
+def test_light_collection_autograd(scaled, T):
+    det, trk, orc = scaled
+    theta = trk.theta().clone().requires_grad_(True)
+    hits = T.LightCollection.apply(theta, trk, 100_000, 7)
+    w = torch.linspace(0.0, 1.0, hits.numel(), dtype=torch.float64, device=hits.device)
+    (hits * w).sum().backward()
+    out = trk.propagate(100_000, seed=7, adjoint=True)
+    J = trk.jacobian(out["adjoint"])
+    want = (J * w[:, None]).sum(0).cpu()
+    torch.testing.assert_close(theta.grad, want, rtol=1e-9, atol=1e-9)
+    assert torch.equal(hits.cpu(), out["det"].double().cpu())
+
+
+def test_adjoint_flag_does_not_change_the_forward(scaled):
+    det, trk, orc = scaled
+    a = trk.propagate(50_000, seed=2)
+    b = trk.propagate(50_000, seed=2, adjoint=True)
+    for k in ("lce", "det", "hist", "fates"):
+        assert torch.equal(a[k], b[k]), k
