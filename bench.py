@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+adjoint cost measurement")
+    ap.add_argument("--no-events", action="store_true", help="skip the batched-events measurement")
     return ap.parse_args()
 
 
@@ -173,6 +174,56 @@ def adjoint_cost(args, n=10_000_000, reps=3):
     return {"workload": "50 cm dual-phase TPC, 61+61 PMTs, thin-disk gate/anode/cathode, 1e7 photons, 7 parameters",
             "fwd_ms": times[False], "fwd_adjoint_ms": times[True], "ratio": times[True] / times[False],
             "fwd_photons_per_s": n / (times[False] / 1e3)}
+
+
+def events_throughput(det, reps=3):
+    """Batched events on the DARWIN-scale mesh: 4096 S1 point sources
+    (log-uniform 1e2..1e5 photons) and 512 S2 segments in the gas gap
+    (log-uniform 1e5..1e6), 2.6e8 photons, per-event per-PMT counts and
+    256 x 1 ns time histograms; launch shape autotuned on a 10 % subset, then
+    one launch captured in a CUDA graph and replayed."""
+    import torch
+    from paper_2203_14354_gb300 import geometry, Tracker
+    from paper_2203_14354_gb300.tracker import autotune_launch
+    ev = geometry.darwin_events(seed=0)
+    trk = Tracker(det)
+    trk.upload_events(ev[::10])
+    sub = trk.alloc_event_results(256, hist=False)
+    best, table = autotune_launch(trk, lambda: trk.propagate_events(seed=1, out=sub, hist=False, sync=False),
+                                  blocks=(3, 4, 5), chunks=(32, 64, 128), reps=2)
+    del sub
+    trk.upload_events(ev)
+    out = trk.alloc_event_results(256, hist=True)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        trk.propagate_events(seed=2, out=out, sync=False)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for v in out.values():
+            v.zero_()
+        trk.propagate_events(seed=2, out=out, sync=False)
+    graph.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    trk.sync()
+    f = out["fates"].cpu().numpy()
+    ms = statistics.median(ts)
+    return {"workload": "4096 S1 + 512 S2 events, DARWIN-scale mesh, one persistent launch under a CUDA graph, "
+                        "per-event per-PMT counts + 257-bin histograms", "events": len(ev),
+            "photons": trk.event_photons, "ms": ms, "photons_per_s": trk.event_photons / (ms / 1e3),
+            "launch": {"blocks_per_sm": best[0], "chunk": best[1]},
+            "autotune_ms": {f"{b}x{c}": round(t, 3) for (b, c), t in table.items()},
+            "lce": float(out["lce"].sum().item()) / trk.event_photons, "escaped": int(f[4]), "geom_err": int(f[6])}
 
 
 def run_reference(args, rank, world):
@@ -311,6 +362,7 @@ def main():
     h2d = ctypes.sizeof(_capi.lxo_source) + ctypes.sizeof(_capi.lxo_run_params)
 
     adjoint = adjoint_cost(args) if (rank == 0 and not args.no_adjoint) else None
+    events = events_throughput(det) if (rank == 0 and not args.no_events) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -346,6 +398,8 @@ def main():
             line["cpu_baseline"] = cpu
         if adjoint is not None:
             line["adjoint"] = adjoint
+        if events is not None:
+            line["events"] = events
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

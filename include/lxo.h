@@ -247,6 +247,40 @@ lxo_status lxo_propagate(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64
 lxo_status lxo_propagate_host(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
                               const lxo_run_params* params, const lxo_results* host_out, void* stream);
 
+/* ---- batched events ----------------------------------------------------
+ * Many sources of uneven photon counts in one persistent launch (the
+ * paper's LCE maps run ~2500 point sources, Sec. 4.1; S1 light from an
+ * interaction point and S2 light along the electron path in the gas gap,
+ * Sec. 1).  Event e's photon i has photon id (e << 32) | i, so its random
+ * stream is that of a single-source lxo_propagate with
+ * photon_id_base = e << 32, and each event is reproducible on its own. */
+typedef struct {
+    int32_t kind;         /* LXO_SRC_POINT, LXO_SRC_SEGMENT or LXO_SRC_BALL */
+    int32_t medium;
+    float center[3];      /* point, segment start or ball centre */
+    float p1[3];          /* segment end */
+    float radius;         /* ball radius */
+    float t0;             /* ns */
+    uint64_t n_photons;   /* < 2^32 */
+} lxo_event;
+
+/* Copies the event table (host [n]) to the device (context-owned, replaces
+ * the previous table).  Synchronous. */
+lxo_status lxo_upload_events(lxo_ctx* ctx, const lxo_event* ev, uint32_t n);
+
+/* Propagates every photon of the uploaded events in one launch.  out (device,
+ * caller-owned, accumulated): lce, det [E*P] (row = event), hist
+ * [E*P*(n_tbins+1)] or NULL (no time histograms), fates [8+M+S] over all
+ * events; per-photon outputs, stats and adjoint must be NULL / off.  Uses only
+ * device-resident tables, so it can be captured in a CUDA graph and replayed.
+ * Asynchronous on `stream`. */
+lxo_status lxo_propagate_events(lxo_ctx* ctx, const lxo_run_params* params, const lxo_results* out, void* stream);
+
+/* Launch shape of the propagation kernels (found by an autotuner):
+ * blocks_per_sm in 1..the occupancy limit (0 = the limit) and photon ids
+ * taken per warp from the work queue, chunk in 1..4096 (0 = 64). */
+lxo_status lxo_set_launch(lxo_ctx* ctx, uint32_t blocks_per_sm, uint32_t chunk);
+
 /* Adjoint (an extension of the paper's method: it has no gradients; the
  * quantities are its Table 2 parameters and the Sec. 2.1 electrode model).
  * The gradient of expected detected hits per channel with respect to

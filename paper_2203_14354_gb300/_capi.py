@@ -41,6 +41,11 @@ class lxo_source(C.Structure):
                 ("pos", C.c_void_p), ("dir", C.c_void_p), ("pol", C.c_void_p)]
 
 
+class lxo_event(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("medium", C.c_int32), ("center", C.c_float * 3), ("p1", C.c_float * 3),
+                ("radius", C.c_float), ("t0", C.c_float), ("n_photons", C.c_uint64)]
+
+
 class lxo_run_params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("max_steps", C.c_uint32), ("n_tbins", C.c_uint32), ("tbin_ns", C.c_float),
                 ("flags", C.c_uint32)]
@@ -81,6 +86,9 @@ _SIGNATURES = {
                                      C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
     "lxo_sync": (C.c_int, [vp, vp]),
     "lxo_set_adjoint": (C.c_int, [vp, vp, C.c_uint32, vp, C.c_uint32]),
+    "lxo_upload_events": (C.c_int, [vp, vp, C.c_uint32]),
+    "lxo_propagate_events": (C.c_int, [vp, C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
+    "lxo_set_launch": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
     "lxo_adjoint_jacobian": (C.c_int, [vp, vp, vp, vp, vp, vp]),
     "lxo_propagate_host_static": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,
                                             C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),

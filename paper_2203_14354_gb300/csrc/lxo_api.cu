@@ -30,7 +30,12 @@ struct lxo_ctx {
     std::vector<lxo_surface> surfs;
     std::vector<lxo_pmt> pmts;
     std::vector<int32_t> adj_mats, adj_surfs;
+    std::vector<lxo_event> events;
+    uint32_t launch_blocks_per_sm = 0, launch_chunk = 64;
     // device
+    lxo::EventDev* d_events = nullptr;
+    unsigned long long* d_ev_prefix = nullptr;
+    uint64_t ev_total = 0;
     float4* d_nodes = nullptr;
     float4* d_tris = nullptr;
     int32_t* d_cells = nullptr;
@@ -183,6 +188,8 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
     }
     p->queue = c->d_queue;
     p->err = c->d_err;
+    p->chunk = c->launch_chunk;
+    p->blocks_per_sm = c->launch_blocks_per_sm;
     for (int m = 0; m < LXO_MAX_MATERIALS; ++m) p->adj_mat_slot[m] = -1;
     for (int q = 0; q < LXO_MAX_SURFACES; ++q) p->adj_surf_slot[q] = -1;
     p->adj_k = 0;
@@ -234,6 +241,8 @@ void lxo_destroy(lxo_ctx* c)
     if (c->d_queue) cudaFree(c->d_queue);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_tally) cudaFree(c->d_tally);
+    if (c->d_events) cudaFree(c->d_events);
+    if (c->d_ev_prefix) cudaFree(c->d_ev_prefix);
     delete c;
 }
 
@@ -502,6 +511,84 @@ lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uin
         host_out->det[i] += hu[P + i];
     }
     for (size_t i = 0; i < P * B; ++i) host_out->hist[i] += hu[2 * P + i];
+    return LXO_OK;
+}
+
+lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (!ev || n == 0) return fail(c, LXO_ERR_ARG, "upload_events: no events");
+    std::vector<lxo::EventDev> h(n);
+    std::vector<unsigned long long> pre(n + 1, 0);
+    for (uint32_t e = 0; e < n; ++e) {
+        const lxo_event& x = ev[e];
+        if (x.kind != LXO_SRC_POINT && x.kind != LXO_SRC_SEGMENT && x.kind != LXO_SRC_BALL)
+            return fail(c, LXO_ERR_ARG, "upload_events: event %u has source kind %d (point, segment or ball only)",
+                        e, x.kind);
+        if (x.n_photons >= (1ull << 32))
+            return fail(c, LXO_ERR_ARG, "upload_events: event %u has %llu photons (< 2^32)", e,
+                        (unsigned long long)x.n_photons);
+        if (x.medium < 0) return fail(c, LXO_ERR_ARG, "upload_events: event %u medium %d", e, x.medium);
+        h[e] = lxo::EventDev{x.kind, x.medium, {x.center[0], x.center[1], x.center[2]}, {x.p1[0], x.p1[1], x.p1[2]},
+                             x.radius, x.t0};
+        pre[e + 1] = pre[e] + x.n_photons;
+    }
+    DeviceGuard g(c->device);
+    if (c->d_events) cudaFree(c->d_events);
+    if (c->d_ev_prefix) cudaFree(c->d_ev_prefix);
+    c->d_events = nullptr;
+    c->d_ev_prefix = nullptr;
+    c->events.clear();
+    CK(cudaMalloc(&c->d_events, sizeof(lxo::EventDev) * n), "upload_events: alloc");
+    CK(cudaMalloc(&c->d_ev_prefix, sizeof(unsigned long long) * (n + 1)), "upload_events: alloc");
+    CK(cudaMemcpy(c->d_events, h.data(), sizeof(lxo::EventDev) * n, cudaMemcpyHostToDevice), "upload_events: copy");
+    CK(cudaMemcpy(c->d_ev_prefix, pre.data(), sizeof(unsigned long long) * (n + 1), cudaMemcpyHostToDevice),
+       "upload_events: copy");
+    c->events.assign(ev, ev + n);
+    c->ev_total = pre[n];
+    return LXO_OK;
+}
+
+lxo_status lxo_propagate_events(lxo_ctx* c, const lxo_run_params* rp, const lxo_results* out, void* stream)
+{
+    if (!c) return LXO_ERR_ARG;
+    lxo_status s = validate(c);
+    if (s) return s;
+    if (c->events.empty()) return fail(c, LXO_ERR_STATE, "propagate_events: no events uploaded");
+    if (!rp) return fail(c, LXO_ERR_ARG, "propagate_events: run params are NULL");
+    if (!out || !out->lce || !out->det || !out->fates)
+        return fail(c, LXO_ERR_ARG, "propagate_events: lce, det and fates buffers are required");
+    if (out->ph_fate || out->ph_detail || out->ph_steps || out->ph_time || out->stats || out->adjoint ||
+        (rp->flags & (LXO_FLAG_STATS | LXO_FLAG_ADJOINT)))
+        return fail(c, LXO_ERR_ARG, "propagate_events: per-photon outputs, stats and adjoint are not supported");
+    for (size_t e = 0; e < c->events.size(); ++e)
+        if (c->events[e].medium >= (int)c->mats.size())
+            return fail(c, LXO_ERR_ARG, "propagate_events: event %zu medium %d >= %zu materials", e,
+                        c->events[e].medium, c->mats.size());
+    lxo_source src{};
+    src.kind = LXO_SRC_POINT;
+    src.medium = c->events[0].medium;
+    lxo::PropParams p;
+    s = fill_params(c, &src, c->ev_total, 0, rp, &p);
+    if (s) return s;
+    p.out = *out;
+    p.n_events = (uint32_t)c->events.size();
+    p.events = c->d_events;
+    p.ev_prefix = c->d_ev_prefix;
+    if (c->ev_total == 0) return LXO_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long), st), "propagate_events: reset queue");
+    CK(lxo::launch_propagate(p, c->device, st), "propagate_events: launch");
+    return LXO_OK;
+}
+
+lxo_status lxo_set_launch(lxo_ctx* c, uint32_t blocks_per_sm, uint32_t chunk)
+{
+    if (!c) return LXO_ERR_ARG;
+    if (blocks_per_sm > 32 || chunk > 4096) return fail(c, LXO_ERR_ARG, "set_launch: blocks_per_sm <= 32, chunk <= 4096");
+    c->launch_blocks_per_sm = blocks_per_sm;
+    c->launch_chunk = chunk ? chunk : 64;
     return LXO_OK;
 }
 

@@ -113,6 +113,11 @@ struct SourceDev {
     const float* pol;
 };
 
+struct EventDev {
+    int kind, medium;
+    float center[3], p1[3], radius, t0;
+};
+
 struct PropParams {
     Scene sc;
     SourceDev src;
@@ -127,6 +132,11 @@ struct PropParams {
     signed char adj_mat_slot[LXO_MAX_MATERIALS]; // tracked material -> index, -1 if not
     signed char adj_surf_slot[LXO_MAX_SURFACES]; // tracked surface -> index, -1 if not
     int adj_n_mats;
+    uint32_t n_events;                 // 0: single source
+    const EventDev* events;            // [n_events]
+    const unsigned long long* ev_prefix;  // [n_events + 1] photon-count prefix sums
+    uint32_t chunk;                    // photon ids per warp grab
+    uint32_t blocks_per_sm;            // 0 = occupancy limit
     unsigned long long* queue;   // scratch: work-queue head
     int* err;                    // scratch: device error word
 };

@@ -433,8 +433,52 @@ __device__ __forceinline__ bool inside_poly(const SourceDev& s, float x, float y
     return x * s.side_cos[k] + y * s.side_sin[k] <= s.apothem;
 }
 
+// Event of global photon index idx (binary search on the prefix sums) and
+// the photon's first state: direction and polarisation as for any source,
+// position from the event's point / segment / ball.
+__device__ Photon make_event_photon(const PropParams& p, uint64_t idx)
+{
+    uint32_t lo = 0, hi = p.n_events;  // find e with prefix[e] <= idx < prefix[e+1]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&p.ev_prefix[mid]) <= idx) lo = mid; else hi = mid;
+    }
+    const EventDev ev = p.events[lo];
+    Photon ph;
+    ph.pid = ((uint64_t)lo << 32) | (uint64_t)(idx - __ldg(&p.ev_prefix[lo]));
+    ph.medium = ev.medium;
+    ph.time = ev.t0;
+    ph.last = LXO_NO_HIT;
+    ph.step = 0;
+    const U4 u = draw4(p.seed, ph.pid, kSourceStep, 0);
+    const float c = 2.0f * u.u0 - 1.0f, sn = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    float sp, cp;
+    sincospif(2.0f * u.u1, &sp, &cp);
+    ph.dir = f3(sn * cp, sn * sp, c);
+    ph.pol = random_pol(ph.dir, u.u2);
+    if (ev.kind == LXO_SRC_SEGMENT) {
+        ph.pos = f3(ev.center[0] + u.u3 * (ev.p1[0] - ev.center[0]), ev.center[1] + u.u3 * (ev.p1[1] - ev.center[1]),
+                    ev.center[2] + u.u3 * (ev.p1[2] - ev.center[2]));
+    } else {
+        ph.pos = f3(ev.center[0], ev.center[1], ev.center[2]);
+        if (ev.kind == LXO_SRC_BALL) {
+            for (int tr = 0; tr < kMaxTries; ++tr) {
+                const U4 w = draw4(p.seed, ph.pid, kSourceStep, 1 + tr);
+                const float x = ev.radius * (2.0f * w.u0 - 1.0f), y = ev.radius * (2.0f * w.u1 - 1.0f),
+                            z = ev.radius * (2.0f * w.u2 - 1.0f);
+                if (x * x + y * y + z * z <= ev.radius * ev.radius) {
+                    ph.pos = f3(ev.center[0] + x, ev.center[1] + y, ev.center[2] + z);
+                    break;
+                }
+            }
+        }
+    }
+    return ph;
+}
+
 __device__ Photon make_photon(const PropParams& p, uint64_t idx)
 {
+    if (p.n_events) return make_event_photon(p, idx);
     const SourceDev& s = p.src;
     Photon ph;
     ph.pid = p.base + idx;
@@ -766,7 +810,7 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
 // persistent propagation kernel
 // ---------------------------------------------------------------------------
 constexpr int kPropThreads = kPropThreadsK;
-constexpr uint32_t kChunk = 64;
+constexpr uint32_t kChunkDefault = 64;
 // tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
 // idle; 5 CTAs of 256 threads per SM (51 registers) hide more L1/L2 latency
 // than 3 CTAs at 80 registers (+22 %) despite a few spills
@@ -791,12 +835,16 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
     if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
     if (fate == LXO_FATE_SURF_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + p.n_mat + detail], 1ull);
     if (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) {
-        atomicAdd(&p.out.lce[detail], 1u);
+        // row of the tallies: the channel, or event * P + channel for batched events
+        const size_t row = p.n_events ? (size_t)(ph.pid >> 32) * p.n_chan + detail : (size_t)detail;
+        atomicAdd(&p.out.lce[row], 1u);
         if (fate == LXO_FATE_DETECTED) {
-            atomicAdd(&p.out.det[detail], 1u);
-            const float b = floorf(ph.time / p.tbin);
-            const uint32_t bin = (b >= (float)p.n_tbins || !(b >= 0.0f)) ? p.n_tbins : (uint32_t)b;
-            atomicAdd(&p.out.hist[(size_t)detail * (p.n_tbins + 1) + bin], 1u);
+            atomicAdd(&p.out.det[row], 1u);
+            if (p.out.hist) {
+                const float b = floorf(ph.time / p.tbin);
+                const uint32_t bin = (b >= (float)p.n_tbins || !(b >= 0.0f)) ? p.n_tbins : (uint32_t)b;
+                atomicAdd(&p.out.hist[row * (p.n_tbins + 1) + bin], 1u);
+            }
         }
     }
     const uint64_t idx = ph.pid - p.base;
@@ -809,7 +857,7 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
 // Persistent photon loop.  A lane whose photon reached its fate stays idle
 // until at least LXO_REFILL_MIN lanes of its warp are idle (or all are); then
 // the idle lanes record their tallies together and take the next photon ids
-// from a warp-local chunk (ballot + prefix popcount), chunks of kChunk ids
+// from a warp-local chunk (ballot + prefix popcount), chunks of p.chunk ids
 // coming from the global work-queue head.  Source sampling and tallies thus
 // run on many lanes at once instead of one lane per iteration.
 template <bool kStats, bool kAdjoint>
@@ -843,14 +891,14 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
             while (need && !exhausted) {
                 if (chunk_next >= chunk_end) {
                     unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)kChunk);
+                    if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)p.chunk);
                     base = __shfl_sync(FULL_MASK, base, 0);
                     if (base >= p.n) {
                         exhausted = true;
                         break;
                     }
                     chunk_next = base;
-                    chunk_end = min(base + kChunk, (unsigned long long)p.n);
+                    chunk_end = min(base + p.chunk, (unsigned long long)p.n);
                 }
                 const uint32_t avail = (uint32_t)(chunk_end - chunk_next);
                 const uint32_t take = min(avail, (uint32_t)__popc(need));
@@ -929,6 +977,7 @@ cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
                       : (adj ? k_propagate<false, true> : k_propagate<false, false>);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPropThreads, 0);
     if (e != cudaSuccess) return e;
+    if (p.blocks_per_sm > 0 && (int)p.blocks_per_sm < per_sm) per_sm = (int)p.blocks_per_sm;
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
     const uint64_t need = (p.n + kPropThreads - 1) / kPropThreads;
     if (need < blocks) blocks = need;

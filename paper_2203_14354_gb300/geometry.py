@@ -801,3 +801,36 @@ def reflector_box(reflectivity=0.8, spec_frac=1.0, half=500.0, z_bot=-100.0, z_t
     src = Source(SRC_POINT, 0, center=(0.0, 0.0, 0.0))
     return Detector("reflector_box", verts, tris, mi, mo, sf, ch, mats, surfs, np.array([1], np.int32),
                     np.array([[0, 0, z_top]], np.float32), src, dict())
+
+
+def darwin_events(seed=0, n_s1=4096, n_s2=512, s1_range=(1e2, 1e5), s2_range=(1e5, 1e6), radius=1300.0,
+                  z_active=(-2597.0, -1.0), z_gap=(2.01, 7.85)):
+    """Batched events in the DARWIN-scale detector: S1-like point sources
+    uniform in the active LXe (inside the 24-gon, z in z_active) with photon
+    counts log-uniform in s1_range, and S2-like sources uniform along a
+    vertical segment in the gas gap between the liquid surface (z = +2) and
+    the anode (z = +8) at (x, y) uniform in the 24-gon, photon counts
+    log-uniform in s2_range (Sec. 1: S1 scintillation at the interaction
+    point, S2 light in the gas).  Returns a list of (Source, n_photons)."""
+    rng = np.random.default_rng(seed)
+    poly = polygon_vertices(24, radius)
+
+    def xy(n):
+        out = []
+        while len(out) < n:
+            p = rng.uniform(-radius, radius, (2 * n, 2))
+            out.extend(p[_inside_convex(p, poly, margin=1.0)].tolist())
+        return np.array(out[:n])
+
+    ev = []
+    p1 = xy(n_s1)
+    z1 = rng.uniform(*z_active, n_s1)
+    c1 = np.exp(rng.uniform(np.log(s1_range[0]), np.log(s1_range[1]), n_s1)).astype(np.int64)
+    for (x, y), z, n in zip(p1, z1, c1):
+        ev.append((Source(SRC_POINT, LXE, center=(float(x), float(y), float(z))), int(n)))
+    p2 = xy(n_s2)
+    c2 = np.exp(rng.uniform(np.log(s2_range[0]), np.log(s2_range[1]), n_s2)).astype(np.int64)
+    for (x, y), n in zip(p2, c2):
+        ev.append((Source(SRC_SEGMENT, GXE, center=(float(x), float(y), z_gap[0]),
+                          p1=(float(x), float(y), z_gap[1])), int(n)))
+    return ev

@@ -267,6 +267,72 @@ class Tracker:
     def sync(self, stream=None):
         self._check(self._L.lxo_sync(self._ctx, _stream(stream)))
 
+    # -- batched events -------------------------------------------------------
+    def upload_events(self, events):
+        """events: list of (Source (POINT / SEGMENT / BALL), n_photons)."""
+        arr = (A.lxo_event * len(events))()
+        for i, (src, n) in enumerate(events):
+            e = arr[i]
+            e.kind, e.medium = int(src.kind), int(src.medium)
+            e.center[:] = [float(x) for x in src.center]
+            e.p1[:] = [float(x) for x in src.p1]
+            e.radius, e.t0, e.n_photons = float(src.radius), float(src.t0), int(n)
+        self._check(self._L.lxo_upload_events(self._ctx, arr, len(events)))
+        self.n_events = len(events)
+        self.event_photons = int(sum(int(n) for _, n in events))
+
+    def alloc_event_results(self, n_tbins=256, hist=True):
+        E, P, dev = self.n_events, self.n_channels, self.device
+        out = dict(lce=torch.zeros((E, P), dtype=torch.int32, device=dev),
+                   det=torch.zeros((E, P), dtype=torch.int32, device=dev),
+                   fates=torch.zeros(self.n_fates, dtype=torch.int64, device=dev))
+        if hist:
+            out["hist"] = torch.zeros((E, P, n_tbins + 1), dtype=torch.int32, device=dev)
+        return out
+
+    def propagate_events(self, seed=0, n_tbins=256, tbin_ns=1.0, max_steps=10000, out=None, hist=True,
+                         stream=None, sync=True):
+        """All uploaded events in one launch; per-event tallies [E, P] (and
+        [E, P, n_tbins+1] time histograms if hist)."""
+        if out is None:
+            out = self.alloc_event_results(n_tbins, hist)
+        rp = A.lxo_run_params(seed, max_steps, n_tbins, tbin_ns, 0)
+        r = A.lxo_results()
+        r.lce, r.det, r.fates = out["lce"].data_ptr(), out["det"].data_ptr(), out["fates"].data_ptr()
+        r.hist = out["hist"].data_ptr() if "hist" in out else None
+        st = _stream(stream)
+        self._check(self._L.lxo_propagate_events(self._ctx, C.byref(rp), C.byref(r), st))
+        if sync:
+            self._check(self._L.lxo_sync(self._ctx, st))
+        return out
+
+    def set_launch(self, blocks_per_sm=0, chunk=0):
+        self._check(self._L.lxo_set_launch(self._ctx, blocks_per_sm, chunk))
+
+
+def autotune_launch(tracker, run, blocks=(2, 3, 4, 5), chunks=(32, 64, 128, 256), reps=2):
+    """Times `run()` (one launch of the workload to tune, on the current
+    stream) for every launch shape and keeps the fastest; returns
+    (blocks_per_sm, chunk, ms) and the table of timings."""
+    table = {}
+    for b in blocks:
+        for c in chunks:
+            tracker.set_launch(b, c)
+            run()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                run()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            table[(b, c)] = min(ts)
+    best = min(table, key=table.get)
+    tracker.set_launch(*best)
+    return (*best, table[best]), table
+
 
 class LightCollection(torch.autograd.Function):
     """Expected detected hits per PMT as a differentiable function of the

@@ -1,0 +1,114 @@
+"""Batched events (lxo_upload_events / lxo_propagate_events) through the C
+ABI: each event's tallies equal a single-source run of its photon ids
+(e << 32) + i bit for bit; statistical parity with the oracle; a CUDA-graph
+replay equals the eager launch; results do not depend on the launch shape."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2203_14354_gb300 import geometry as g
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small_events():
+    from paper_2203_14354_gb300 import Tracker
+    det = g.small_tpc()
+    rng = np.random.default_rng(4)
+    ev = []
+    for k in range(40):
+        x, y = rng.uniform(-60, 60, 2)
+        z = rng.uniform(-95, -5)
+        n = int(np.exp(rng.uniform(np.log(50), np.log(20000))))
+        if k % 5 == 4:
+            ev.append((g.Source(g.SRC_SEGMENT, g.GXE, center=(x, y, 0.5), p1=(x, y, 4.5)), n))
+        elif k % 7 == 6:
+            ev.append((g.Source(g.SRC_BALL, g.LXE, center=(x, y, z), radius=3.0), n))
+        else:
+            ev.append((g.Source(g.SRC_POINT, g.LXE, center=(x, y, z)), n))
+    ev.append((g.Source(g.SRC_POINT, g.LXE, center=(0.0, 0.0, -50.0)), 0))  # an empty event
+    trk = Tracker(det)
+    trk.upload_events(ev)
+    return det, trk, ev
+
+
+def test_events_equal_single_source_runs(small_events):
+    det, trk, ev = small_events
+    out = trk.propagate_events(seed=9, n_tbins=64)
+    assert int(out["fates"][:7].sum()) == sum(n for _, n in ev)
+    fates_sum = torch.zeros_like(out["fates"])
+    for e, (src, n) in enumerate(ev):
+        one = trk.propagate(n, base=e << 32, seed=9, source=src, n_tbins=64)
+        assert torch.equal(one["lce"], out["lce"][e]), e
+        assert torch.equal(one["det"], out["det"][e]), e
+        assert torch.equal(one["hist"], out["hist"][e]), e
+        fates_sum += one["fates"]
+    assert torch.equal(fates_sum, out["fates"])
+
+
+def test_events_parity_with_oracle(small_events):
+    det, trk, ev = small_events
+    out = trk.propagate_events(seed=9, n_tbins=64)
+    orc = O.Oracle(det)
+    lce_o = np.zeros((len(ev), det.n_pmts))
+    for e, (src, n) in enumerate(ev):
+        if n:
+            lce_o[e] = orc.propagate(n, base=e << 32, seed=9, src=src)["lce"]
+    lce_g = out["lce"].cpu().numpy()
+    tot = lce_o.sum()
+    assert abs(lce_g.sum() - tot) < 0.02 * tot
+    for e, (_, n) in enumerate(ev):
+        if n > 2000:
+            a, b = lce_g[e].sum(), lce_o[e].sum()
+            assert abs(a - b) <= 4 * np.sqrt(2 * max(b, 1)) + 0.01 * b, e
+
+
+def test_events_cuda_graph_and_launch_shape(small_events):
+    det, trk, ev = small_events
+    ref = trk.propagate_events(seed=5, hist=False)
+    out = trk.alloc_event_results(hist=False)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        trk.propagate_events(seed=5, out=out, hist=False, sync=False)  # warm-up outside the graph
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for v in out.values():
+            v.zero_()
+        trk.propagate_events(seed=5, out=out, hist=False, sync=False)
+    for _ in range(3):
+        graph.replay()
+        torch.cuda.synchronize()
+        for k in ("lce", "det", "fates"):
+            assert torch.equal(out[k], ref[k]), k
+    trk.sync()
+    for b, c in ((1, 16), (3, 256), (0, 0)):
+        trk.set_launch(b, c)
+        o = trk.propagate_events(seed=5, hist=False)
+        for k in ("lce", "det", "fates"):
+            assert torch.equal(o[k], ref[k]), (b, c, k)
+
+
+def test_darwin_events_subset(tmp_path):
+    from paper_2203_14354_gb300 import Tracker
+    det = g.darwin()
+    ev = g.darwin_events(seed=1)
+    sub = ev[:48] + ev[4096:4100]
+    trk = Tracker(det)
+    trk.upload_events(sub)
+    out = trk.propagate_events(seed=3, n_tbins=256)
+    assert int(out["fates"][:7].sum()) == sum(n for _, n in sub)
+    assert int(out["fates"][4]) + int(out["fates"][6]) <= 1e-4 * sum(n for _, n in sub) + 2
+    for e in (0, 7, 48, 50):
+        src, n = sub[e]
+        one = trk.propagate(n, base=e << 32, seed=3, source=src, n_tbins=256)
+        assert torch.equal(one["det"], out["det"][e]) and torch.equal(one["hist"], out["hist"][e])
+    # S2 light in the gas reaches the top array far more than S1 light from deep in the LXe
+    top = torch.from_numpy(det.pmt_array == 1).to(out["lce"].device)
+    s2 = out["lce"][48:][:, top].sum() / out["lce"][48:].sum()
+    s1 = out["lce"][:48][:, top].sum() / out["lce"][:48].sum().clamp(min=1)
+    assert float(s2) > float(s1)
