@@ -271,7 +271,8 @@ lxo_status lxo_upload_events(lxo_ctx* ctx, const lxo_event* ev, uint32_t n);
 /* Propagates every photon of the uploaded events in one launch.  out (device,
  * caller-owned, accumulated): lce, det [E*P] (row = event), hist
  * [E*P*(n_tbins+1)] or NULL (no time histograms), fates [8+M+S] over all
- * events; per-photon outputs, stats and adjoint must be NULL / off.  Uses only
+ * events, and with LXO_FLAG_ADJOINT adjoint [E*P*K]; per-photon outputs and
+ * stats must be NULL / off.  Uses only
  * device-resident tables, so it can be captured in a CUDA graph and replayed.
  * Asynchronous on `stream`. */
 lxo_status lxo_propagate_events(lxo_ctx* ctx, const lxo_run_params* params, const lxo_results* out, void* stream);
@@ -300,12 +301,14 @@ lxo_status lxo_set_launch(lxo_ctx* ctx, uint32_t blocks_per_sm, uint32_t chunk);
 lxo_status lxo_set_adjoint(lxo_ctx* ctx, const int32_t* mats, uint32_t n_mats, const int32_t* surfs,
                            uint32_t n_surfs);
 
-/* J [P*Q] (device, row = channel, Q = 2*n_mats + n_surfs) from the tally
- * sums [P*K] (device) at the current material / surface values; if g (device
- * [P]) and grad (device [Q]) are not NULL, also grad = J^T g (the
- * vector-Jacobian product of a backward pass).  Asynchronous on `stream`. */
-lxo_status lxo_adjoint_jacobian(lxo_ctx* ctx, const double* tally_sums, double* J, const double* g, double* grad,
-                                void* stream);
+/* J [R*Q] (device, Q = 2*n_mats + n_surfs) from tally sums [R*K] (device) at
+ * the current material / surface values, R = n_rows (0 = P, one row per
+ * channel; E*P for the sums of lxo_propagate_events, row = event*P +
+ * channel); if g (device [R]) and grad (device [Q]) are not NULL, also
+ * grad = J^T g (the vector-Jacobian product of a backward pass).
+ * Asynchronous on `stream`. */
+lxo_status lxo_adjoint_jacobian(lxo_ctx* ctx, const double* tally_sums, uint32_t n_rows, double* J, const double* g,
+                                double* grad, void* stream);
 
 /* Waits for `stream` and reports a device-side fault recorded since the last
  * lxo_sync (then clears it). */

@@ -89,7 +89,7 @@ _SIGNATURES = {
     "lxo_upload_events": (C.c_int, [vp, vp, C.c_uint32]),
     "lxo_propagate_events": (C.c_int, [vp, C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
     "lxo_set_launch": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
-    "lxo_adjoint_jacobian": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+    "lxo_adjoint_jacobian": (C.c_int, [vp, vp, C.c_uint32, vp, vp, vp, vp]),
     "lxo_propagate_host_static": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,
                                             C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
 }

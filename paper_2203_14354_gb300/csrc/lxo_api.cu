@@ -558,9 +558,10 @@ lxo_status lxo_propagate_events(lxo_ctx* c, const lxo_run_params* rp, const lxo_
     if (!rp) return fail(c, LXO_ERR_ARG, "propagate_events: run params are NULL");
     if (!out || !out->lce || !out->det || !out->fates)
         return fail(c, LXO_ERR_ARG, "propagate_events: lce, det and fates buffers are required");
-    if (out->ph_fate || out->ph_detail || out->ph_steps || out->ph_time || out->stats || out->adjoint ||
-        (rp->flags & (LXO_FLAG_STATS | LXO_FLAG_ADJOINT)))
-        return fail(c, LXO_ERR_ARG, "propagate_events: per-photon outputs, stats and adjoint are not supported");
+    if (out->ph_fate || out->ph_detail || out->ph_steps || out->ph_time || out->stats || (rp->flags & LXO_FLAG_STATS))
+        return fail(c, LXO_ERR_ARG, "propagate_events: per-photon outputs and stats are not supported");
+    if ((rp->flags & LXO_FLAG_ADJOINT) && !out->adjoint)
+        return fail(c, LXO_ERR_ARG, "propagate_events: LXO_FLAG_ADJOINT needs the adjoint buffer");
     for (size_t e = 0; e < c->events.size(); ++e)
         if (c->events[e].medium >= (int)c->mats.size())
             return fail(c, LXO_ERR_ARG, "propagate_events: event %zu medium %d >= %zu materials", e,
@@ -617,13 +618,17 @@ lxo_status lxo_set_adjoint(lxo_ctx* c, const int32_t* mats, uint32_t n_mats, con
     return LXO_OK;
 }
 
-lxo_status lxo_adjoint_jacobian(lxo_ctx* c, const double* sums, double* J, const double* g, double* grad, void* stream)
+lxo_status lxo_adjoint_jacobian(lxo_ctx* c, const double* sums, uint32_t n_rows, double* J, const double* g,
+                                double* grad, void* stream)
 {
     if (!c) return LXO_ERR_ARG;
     if (!sums || !J || (!g) != (!grad)) return fail(c, LXO_ERR_ARG, "adjoint_jacobian: NULL array");
     const int nm = (int)c->adj_mats.size(), ns = (int)c->adj_surfs.size();
-    const int K = 2 * (nm + ns), Q = 2 * nm + ns, P = (int)c->pmts.size();
+    const int K = 2 * (nm + ns), Q = 2 * nm + ns;
+    const int P = n_rows ? (int)n_rows : (int)c->pmts.size();
     if (K == 0 || P == 0) return fail(c, LXO_ERR_STATE, "adjoint_jacobian: no tracked parameters or no PMTs");
+    if ((uint64_t)P * (uint64_t)Q > (uint64_t)INT32_MAX)
+        return fail(c, LXO_ERR_ARG, "adjoint_jacobian: %u rows x %d parameters exceed 2^31 entries", n_rows, Q);
     lxo::AdjCoef coef[2 * LXO_ADJ_MAX_MATERIALS + LXO_ADJ_MAX_SURFACES];
     for (int i = 0; i < nm; ++i) {
         const lxo_material& m = c->mats[c->adj_mats[i]];

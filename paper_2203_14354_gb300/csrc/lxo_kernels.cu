@@ -827,16 +827,16 @@ template <bool kAdjoint>
 __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s_f, const Photon& ph, int fate,
                                       int detail, const float* tl)
 {
+    // row of the per-channel tallies: the channel, or event * P + channel for batched events
+    const size_t row = p.n_events ? (size_t)(ph.pid >> 32) * p.n_chan + detail : (size_t)detail;
     if (kAdjoint && fate == LXO_FATE_DETECTED)
         for (int k = 0; k < p.adj_k; ++k)
-            atomicAdd(&p.out.adjoint[(size_t)detail * p.adj_k + k], (double)tl[k * kPropThreads]);
+            atomicAdd(&p.out.adjoint[row * p.adj_k + k], (double)tl[k * kPropThreads]);
     atomicAdd(&s_f[fate], 1ull);
     atomicAdd(&s_f[7], (unsigned long long)ph.step);
     if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
     if (fate == LXO_FATE_SURF_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + p.n_mat + detail], 1ull);
     if (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) {
-        // row of the tallies: the channel, or event * P + channel for batched events
-        const size_t row = p.n_events ? (size_t)(ph.pid >> 32) * p.n_chan + detail : (size_t)detail;
         atomicAdd(&p.out.lce[row], 1u);
         if (fate == LXO_FATE_DETECTED) {
             atomicAdd(&p.out.det[row], 1u);

@@ -834,3 +834,15 @@ def darwin_events(seed=0, n_s1=4096, n_s2=512, s1_range=(1e2, 1e5), s2_range=(1e
         ev.append((Source(SRC_SEGMENT, GXE, center=(float(x), float(y), z_gap[0]),
                           p1=(float(x), float(y), z_gap[1])), int(n)))
     return ev
+
+
+def calibration_sources(n_photons, n_x=16, n_z=16, spacing=100.0, z_center=-1299.0, medium=LXE):
+    """Point sources for a calibration fit: an n_x by n_z grid with ``spacing``
+    mm pitch in the vertical plane y = 0, centred on (0, 0, z_center), each
+    emitting ``n_photons`` isotropically (the LCE(R, Z) maps of Sec. 3 sample
+    the active volume on such a grid).  The defaults give 256 sources on a
+    10 cm grid around the middle of the DARWIN-scale drift volume.  Returns a
+    list of (Source, n_photons)."""
+    xs = (np.arange(n_x) - (n_x - 1) / 2.0) * spacing
+    zs = z_center + (np.arange(n_z) - (n_z - 1) / 2.0) * spacing
+    return [(Source(SRC_POINT, medium, center=(float(x), 0.0, float(z))), int(n_photons)) for z in zs for x in xs]

@@ -166,14 +166,17 @@ class Tracker:
     def jacobian(self, sums, g=None, stream=None):
         """J [P, Q] (and grad = J^T g [Q] if g is given) from adjoint tally sums
         [P, K] at the current parameter values, computed on the device."""
-        sums = sums.contiguous()
-        J = torch.empty((self.n_channels, self.n_params), dtype=torch.float64, device=self.device)
+        shape = sums.shape[:-1]
+        sums = sums.reshape(-1, self.n_tallies).contiguous()
+        rows = sums.shape[0]
+        J = torch.empty((rows, self.n_params), dtype=torch.float64, device=self.device)
         grad = None
         if g is not None:
-            g = g.to(device=self.device, dtype=torch.float64).contiguous()
+            g = g.reshape(-1).to(device=self.device, dtype=torch.float64).contiguous()
             grad = torch.empty(self.n_params, dtype=torch.float64, device=self.device)
-        self._check(self._L.lxo_adjoint_jacobian(self._ctx, _ptr(sums), _ptr(J), _ptr(g), _ptr(grad),
+        self._check(self._L.lxo_adjoint_jacobian(self._ctx, _ptr(sums), rows, _ptr(J), _ptr(g), _ptr(grad),
                                                  _stream(stream)))
+        J = J.reshape(*shape, self.n_params)
         return J if g is None else (J, grad)
 
     # -- geometry query -----------------------------------------------------
@@ -281,25 +284,29 @@ class Tracker:
         self.n_events = len(events)
         self.event_photons = int(sum(int(n) for _, n in events))
 
-    def alloc_event_results(self, n_tbins=256, hist=True):
+    def alloc_event_results(self, n_tbins=256, hist=True, adjoint=False):
         E, P, dev = self.n_events, self.n_channels, self.device
         out = dict(lce=torch.zeros((E, P), dtype=torch.int32, device=dev),
                    det=torch.zeros((E, P), dtype=torch.int32, device=dev),
                    fates=torch.zeros(self.n_fates, dtype=torch.int64, device=dev))
         if hist:
             out["hist"] = torch.zeros((E, P, n_tbins + 1), dtype=torch.int32, device=dev)
+        if adjoint:
+            out["adjoint"] = torch.zeros((E, P, self.n_tallies), dtype=torch.float64, device=dev)
         return out
 
     def propagate_events(self, seed=0, n_tbins=256, tbin_ns=1.0, max_steps=10000, out=None, hist=True,
-                         stream=None, sync=True):
+                         stream=None, sync=True, adjoint=False):
         """All uploaded events in one launch; per-event tallies [E, P] (and
-        [E, P, n_tbins+1] time histograms if hist)."""
+        [E, P, n_tbins+1] time histograms if hist, adjoint sums [E, P, K] if
+        adjoint)."""
         if out is None:
-            out = self.alloc_event_results(n_tbins, hist)
-        rp = A.lxo_run_params(seed, max_steps, n_tbins, tbin_ns, 0)
+            out = self.alloc_event_results(n_tbins, hist, adjoint)
+        rp = A.lxo_run_params(seed, max_steps, n_tbins, tbin_ns, A.LXO_FLAG_ADJOINT if adjoint else 0)
         r = A.lxo_results()
         r.lce, r.det, r.fates = out["lce"].data_ptr(), out["det"].data_ptr(), out["fates"].data_ptr()
         r.hist = out["hist"].data_ptr() if "hist" in out else None
+        r.adjoint = out["adjoint"].data_ptr() if adjoint else None
         st = _stream(stream)
         self._check(self._L.lxo_propagate_events(self._ctx, C.byref(rp), C.byref(r), st))
         if sync:
@@ -357,3 +364,26 @@ class LightCollection(torch.autograd.Function):
         tr.set_theta(ctx.theta)
         _, grad = tr.jacobian(sums, g)
         return grad.to(ctx.theta.device), None, None, None, None, None
+
+
+class EventLightCollection(torch.autograd.Function):
+    """Expected detected hits per (event, PMT) [E, P] of the uploaded events
+    as a differentiable function of the tracked parameters theta; one
+    batched launch forward, the adjoint kernels backward."""
+
+    @staticmethod
+    def forward(ctx, theta, tracker, seed=0):
+        tracker.set_theta(theta)
+        out = tracker.propagate_events(seed=seed, hist=False, adjoint=True)
+        ctx.tracker = tracker
+        ctx.theta = theta.detach().clone()
+        ctx.save_for_backward(out["adjoint"])
+        return out["det"].to(torch.float64)
+
+    @staticmethod
+    def backward(ctx, g):
+        (sums,) = ctx.saved_tensors
+        tr = ctx.tracker
+        tr.set_theta(ctx.theta)
+        _, grad = tr.jacobian(sums, g)
+        return grad.to(ctx.theta.device), None, None
