@@ -266,7 +266,7 @@ def main():
         return
     import torch
     import torch.distributed as dist
-    from paper_2203_14354_gb300 import geometry, Tracker
+    from paper_2203_14354_gb300 import analysis, geometry, Tracker
 
     if world > 1:
         torch.cuda.set_device(local)
@@ -316,6 +316,7 @@ def main():
     kern_ms = [a.elapsed_time(b) for a, b in zip(k_start, k_end)]
     fates = out["fates"].cpu().numpy()
     lce = out["lce"].cpu().numpy()
+    t90 = analysis.t90(out["hist"].cpu().numpy(), 1.0)
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -361,6 +362,13 @@ def main():
     from paper_2203_14354_gb300 import _capi
     h2d = ctypes.sizeof(_capi.lxo_source) + ctypes.sizeof(_capi.lxo_run_params)
 
+    # t90 with the nuclear-recoil scintillation time profile (untimed side run, 1e7 photons)
+    t90_nr = None
+    if rank == 0:
+        nr = trk.propagate(min(n, 10_000_000), base=base0 + 10**12, seed=3,
+                           source=det.source.with_profile(geometry.NR_PROFILE))
+        t90_nr = analysis.t90(nr["hist"].cpu().numpy(), 1.0)
+
     adjoint = adjoint_cost(args) if (rank == 0 and not args.no_adjoint) else None
     events = events_throughput(det) if (rank == 0 and not args.no_events) else None
 
@@ -391,7 +399,8 @@ def main():
             "gpu_launches": args.steps * 1,
             "clocks": clk.summary(),
             "physics": {"lce": float(lce.sum()) / n, "steps_per_photon": float(fates[7]) / n,
-                        "escaped": int(fates[4]), "geom_err": int(fates[6]), "truncated": int(fates[5])},
+                        "escaped": int(fates[4]), "geom_err": int(fates[6]), "truncated": int(fates[5]),
+                        "t90_ns": t90, "t90_nr_profile_ns": t90_nr},
             "setup_s": setup_s, "bvh": {k: v for k, v in trk.bvh_info.items()},
         }
         if cpu is not None:

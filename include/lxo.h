@@ -36,6 +36,9 @@
  * u0 -> absorption distance -L_abs ln u0, u1 -> Rayleigh distance
  * -L_ray ln u1, u2 -> first surface decision, u3 -> second surface decision;
  * draw 1 (and 2, 3, ... for Rayleigh rejection tries) gives new directions.
+ * The emission-time draw of a source with a scintillation time profile is
+ * (step 0xFFFFFFFF, draw 0xFFFFFFFF): u0 < singlet_frac picks the singlet
+ * component, and the delay is -tau ln u1 of the component picked.
  */
 #ifndef LXO_H
 #define LXO_H
@@ -123,6 +126,14 @@ typedef struct {
     float center[3];
     float p1[3];
     float t0;             /* ns */
+    /* scintillation time profile (Sec. 2.2, Table 2: two exponential decay
+     * components): emission at t0 + a delay drawn from the singlet component
+     * (time constant tau_singlet_ns) with probability singlet_frac, else from
+     * the triplet component (tau_triplet_ns).  Both constants 0: every photon
+     * starts at t0.  A constant must be >= 0 and singlet_frac in [0, 1]. */
+    float singlet_frac;
+    float tau_singlet_ns;
+    float tau_triplet_ns;
     const float* pos;     /* EXPLICIT only, device [n*3] */
     const float* dir;     /* EXPLICIT only, device [n*3], unit */
     const float* pol;     /* EXPLICIT only, device [n*3], unit, made perpendicular to dir */
@@ -231,9 +242,10 @@ lxo_status lxo_trace_rays(lxo_ctx* ctx, const float* org, const float* dir, cons
                           const float* tmax, uint32_t n, uint32_t* hit, float* t, void* stream);
 
 /* The first state of photons base .. base+n-1 from a source: device arrays
- * pos, dir, pol [n*3] (float). */
+ * pos, dir, pol [n*3] (float) and, if not NULL, the emission time [n] (ns;
+ * t0 plus the delay of the source's scintillation time profile). */
 lxo_status lxo_sample_source(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
-                             uint64_t seed, float* pos, float* dir, float* pol, void* stream);
+                             uint64_t seed, float* pos, float* dir, float* pol, float* time, void* stream);
 
 /* Propagates photons base .. base+n-1 to their fates and accumulates the
  * tallies into `out` (device buffers, caller-owned, zeroed by the caller).
@@ -261,6 +273,10 @@ typedef struct {
     float p1[3];          /* segment end */
     float radius;         /* ball radius */
     float t0;             /* ns */
+    float singlet_frac;   /* scintillation time profile, as in lxo_source */
+    float tau_singlet_ns;
+    float tau_triplet_ns;
+    float reserved;
     uint64_t n_photons;   /* < 2^32 */
 } lxo_event;
 

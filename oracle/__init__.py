@@ -53,7 +53,7 @@ def lib():
         L.orc_set_channels.argtypes = [C.c_void_p, C.c_int]
         L.orc_trace.argtypes = [C.c_void_p, C.c_uint64, f32p, f32p, C.c_void_p, C.c_void_p, u32p, f32p, C.c_int]
         L.orc_sample_source.argtypes = [C.c_void_p, C.POINTER(_Source), C.c_uint64, C.c_uint64, C.c_uint64,
-                                        f64p, f64p, f64p, i32p]
+                                        f64p, f64p, f64p, i32p, f64p]
         L.orc_propagate.restype = C.c_int
         L.orc_propagate.argtypes = [C.c_void_p, C.POINTER(_Source), C.c_uint64, C.c_uint64, C.c_uint64,
                                     C.c_uint32, C.c_double, C.c_uint32, C.POINTER(_Results), C.c_int]
@@ -79,7 +79,8 @@ def _ptr(a):
 
 def source_array(src) -> np.ndarray:
     return np.array([src.kind, src.medium, src.n_sides, src.radius, src.phase, src.z_min, src.z_max,
-                     *src.center, *src.p1, src.t0], np.float64)
+                     *src.center, *src.p1, src.t0, src.singlet_frac, src.tau_singlet_ns, src.tau_triplet_ns],
+                    np.float64)
 
 
 class Oracle:
@@ -156,12 +157,14 @@ class Oracle:
             s.explicit_pos, s.explicit_dir, s.explicit_pol = _ptr(pos), _ptr(dir), _ptr(pol)
         return s, keep
 
-    def sample_source(self, n, base=0, seed=0, src=None, explicit=None):
+    def sample_source(self, n, base=0, seed=0, src=None, explicit=None, time=False):
+        """First photon states (pos, dir, pol [n, 3], medium [n]; and emission times [n] if time)."""
         s, keep = self._source(src or self.det.source, explicit)
         pos = np.empty((n, 3)); dir = np.empty((n, 3)); pol = np.empty((n, 3))
         med = np.empty(n, np.int32)
-        lib().orc_sample_source(self._s, C.byref(s), n, base, seed, pos, dir, pol, med)
-        return pos, dir, pol, med
+        t = np.empty(n)
+        lib().orc_sample_source(self._s, C.byref(s), n, base, seed, pos, dir, pol, med, t)
+        return (pos, dir, pol, med, t) if time else (pos, dir, pol, med)
 
     def propagate(self, n, base=0, seed=0, src=None, explicit=None, max_steps=10000, tbin_ns=1.0,
                   n_tbins=1000, per_photon=False, threads=None, adjoint=False):

@@ -611,6 +611,16 @@ static void source_photon(const orc_source* src, uint64_t pid, uint64_t idx, uin
     int kind = (int)p[0];
     *medium = (int)p[1];
     *t0 = p[13];
+    /* scintillation time profile (Sec. 2.2, Table 2): the delay after t0
+     * follows the singlet exponential (constant p[15]) with probability
+     * p[14], else the triplet one (p[16]); own draw (source step, last draw
+     * index): u0 picks the component, u1 the exponential delay */
+    if (p[15] != 0.0 || p[16] != 0.0) {
+        double w[4];
+        draw4(seed, pid, SOURCE_STEP, 0xFFFFFFFFu, w);
+        double tau = w[0] < p[14] ? p[15] : p[16];
+        *t0 += -tau * log(w[1]);
+    }
     if (kind == ORC_SRC_EXPLICIT) {
         for (int a = 0; a < 3; ++a) {
             pos[a] = src->explicit_pos[3 * idx + a];
@@ -663,7 +673,7 @@ static void source_photon(const orc_source* src, uint64_t pid, uint64_t idx, uin
 }
 
 void orc_sample_source(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
-                       double* pos, double* dir, double* pol, int* medium)
+                       double* pos, double* dir, double* pol, int* medium, double* time)
 {
     (void)s;
     for (uint64_t i = 0; i < n; ++i) {
@@ -671,6 +681,7 @@ void orc_sample_source(const orc_scene* s, const orc_source* src, uint64_t n, ui
         int m;
         source_photon(src, base + i, i, seed, &pos[3 * i], &dir[3 * i], &pol[3 * i], &m, &t0);
         if (medium) medium[i] = m;
+        if (time) time[i] = t0;
     }
 }
 

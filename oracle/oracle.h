@@ -58,7 +58,9 @@ void orc_trace(const orc_scene* s, uint64_t n, const float* org, const float* di
 
 /* source description packed as doubles:
  * [0] kind [1] medium [2] n_sides [3] radius [4] phase [5] z_min [6] z_max
- * [7..9] center [10..12] p1 [13] t0.  explicit_* used for ORC_SRC_EXPLICIT ([n*3] each). */
+ * [7..9] center [10..12] p1 [13] t0 [14] singlet fraction [15] singlet and
+ * [16] triplet time constants (ns; both 0 = no emission delay).
+ * explicit_* used for ORC_SRC_EXPLICIT ([n*3] each). */
 typedef struct {
     const double* src;
     const float* explicit_pos;
@@ -66,9 +68,10 @@ typedef struct {
     const float* explicit_pol;
 } orc_source;
 
-/* source sampling only (first photon state), positions/dirs/pols [n*3] */
+/* source sampling only (first photon state), positions/dirs/pols [n*3];
+ * medium [n] and emission time [n] (ns) may be NULL */
 void orc_sample_source(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
-                       double* pos, double* dir, double* pol, int* medium);
+                       double* pos, double* dir, double* pol, int* medium, double* time);
 
 typedef struct {
     uint64_t* lce;        /* [P] photocathode arrivals */

@@ -38,12 +38,15 @@ class lxo_source(C.Structure):
     _fields_ = [("kind", C.c_int32), ("medium", C.c_int32), ("n_sides", C.c_int32), ("reserved", C.c_int32),
                 ("radius", C.c_float), ("phase", C.c_float), ("z_min", C.c_float), ("z_max", C.c_float),
                 ("center", C.c_float * 3), ("p1", C.c_float * 3), ("t0", C.c_float),
+                ("singlet_frac", C.c_float), ("tau_singlet_ns", C.c_float), ("tau_triplet_ns", C.c_float),
                 ("pos", C.c_void_p), ("dir", C.c_void_p), ("pol", C.c_void_p)]
 
 
 class lxo_event(C.Structure):
     _fields_ = [("kind", C.c_int32), ("medium", C.c_int32), ("center", C.c_float * 3), ("p1", C.c_float * 3),
-                ("radius", C.c_float), ("t0", C.c_float), ("n_photons", C.c_uint64)]
+                ("radius", C.c_float), ("t0", C.c_float), ("singlet_frac", C.c_float),
+                ("tau_singlet_ns", C.c_float), ("tau_triplet_ns", C.c_float), ("reserved", C.c_float),
+                ("n_photons", C.c_uint64)]
 
 
 class lxo_run_params(C.Structure):
@@ -79,7 +82,8 @@ _SIGNATURES = {
     "lxo_set_pmts": (C.c_int, [vp, C.POINTER(lxo_pmt), C.c_uint32]),
     "lxo_build_bvh": (C.c_int, [vp, C.POINTER(lxo_bvh_params), C.POINTER(lxo_bvh_info)]),
     "lxo_trace_rays": (C.c_int, [vp, vp, vp, vp, vp, C.c_uint32, vp, vp, vp]),
-    "lxo_sample_source": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, vp, vp]),
+    "lxo_sample_source": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, vp, vp,
+                                     vp]),
     "lxo_propagate": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64, C.POINTER(lxo_run_params),
                                 C.POINTER(lxo_results), vp]),
     "lxo_propagate_host": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,

@@ -151,6 +151,10 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
                     lxo::kMaxPolySides);
     if (src->kind == LXO_SRC_EXPLICIT && (!src->pos || !src->dir || !src->pol))
         return fail(c, LXO_ERR_ARG, "explicit source needs pos, dir and pol device arrays");
+    if (!(src->singlet_frac >= 0.0f && src->singlet_frac <= 1.0f) || !(src->tau_singlet_ns >= 0.0f) ||
+        !(src->tau_triplet_ns >= 0.0f))
+        return fail(c, LXO_ERR_ARG, "source time profile: singlet_frac %g not in [0, 1] or a negative constant",
+                    src->singlet_frac);
     lxo::SourceDev& sd = p->src;
     sd.kind = src->kind;
     sd.medium = src->medium;
@@ -159,6 +163,7 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
     sd.z_min = src->z_min;
     sd.z_max = src->z_max;
     sd.t0 = src->t0;
+    sd.prof = lxo::TimeProfile{src->singlet_frac, src->tau_singlet_ns, src->tau_triplet_ns};
     for (int a = 0; a < 3; ++a) {
         sd.center[a] = src->center[a];
         sd.p1[a] = src->p1[a];
@@ -425,7 +430,7 @@ lxo_status lxo_trace_rays(lxo_ctx* c, const float* org, const float* dir, const 
 }
 
 lxo_status lxo_sample_source(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, uint64_t seed,
-                             float* pos, float* dir, float* pol, void* stream)
+                             float* pos, float* dir, float* pol, float* time, void* stream)
 {
     if (!c) return LXO_ERR_ARG;
     if (c->mats.empty()) return fail(c, LXO_ERR_STATE, "sample_source: no materials set");
@@ -436,7 +441,7 @@ lxo_status lxo_sample_source(lxo_ctx* c, const lxo_source* src, uint64_t n, uint
     lxo_status s = fill_params(c, src, n, base, &rp, &p);
     if (s) return s;
     DeviceGuard g(c->device);
-    CK(lxo::launch_sample_source(p, pos, dir, pol, (cudaStream_t)stream), "sample_source");
+    CK(lxo::launch_sample_source(p, pos, dir, pol, time, (cudaStream_t)stream), "sample_source");
     return LXO_OK;
 }
 
@@ -529,8 +534,12 @@ lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n)
             return fail(c, LXO_ERR_ARG, "upload_events: event %u has %llu photons (< 2^32)", e,
                         (unsigned long long)x.n_photons);
         if (x.medium < 0) return fail(c, LXO_ERR_ARG, "upload_events: event %u medium %d", e, x.medium);
+        if (!(x.singlet_frac >= 0.0f && x.singlet_frac <= 1.0f) || !(x.tau_singlet_ns >= 0.0f) ||
+            !(x.tau_triplet_ns >= 0.0f))
+            return fail(c, LXO_ERR_ARG, "upload_events: event %u time profile (f %g, tau %g, %g)", e, x.singlet_frac,
+                        x.tau_singlet_ns, x.tau_triplet_ns);
         h[e] = lxo::EventDev{x.kind, x.medium, {x.center[0], x.center[1], x.center[2]}, {x.p1[0], x.p1[1], x.p1[2]},
-                             x.radius, x.t0};
+                             x.radius, x.t0, {x.singlet_frac, x.tau_singlet_ns, x.tau_triplet_ns}};
         pre[e + 1] = pre[e] + x.n_photons;
     }
     DeviceGuard g(c->device);

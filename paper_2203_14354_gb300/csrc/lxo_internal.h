@@ -102,9 +102,16 @@ struct Scene {
     ClusterDev clusters[kMaxClusters];
 };
 
+// Emission-time profile: delay -tau ln u, tau = tau_s with probability f_s,
+// else tau_t; all zero = no delay.
+struct TimeProfile {
+    float f_s, tau_s, tau_t;
+};
+
 struct SourceDev {
     int kind, medium, n_sides;
     float radius, z_min, z_max, apothem, t0;
+    TimeProfile prof;
     float phase_turns;    // polygon phase / (2 pi)
     float center[3], p1[3];
     float side_cos[kMaxPolySides], side_sin[kMaxPolySides];
@@ -116,6 +123,7 @@ struct SourceDev {
 struct EventDev {
     int kind, medium;
     float center[3], p1[3], radius, t0;
+    TimeProfile prof;
 };
 
 struct PropParams {
@@ -144,7 +152,7 @@ struct PropParams {
 // kernel launchers (lxo_kernels.cu)
 cudaError_t launch_trace(const Scene& sc, const float* org, const float* dir, const uint32_t* skip,
                          const float* tmax, uint32_t n, uint32_t* hit, float* t, int* err, cudaStream_t st);
-cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, cudaStream_t st);
+cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, float* time, cudaStream_t st);
 cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st);
 
 struct AdjCoef {   // per parameter q: J[c][q] = a * sums[c][ia] + b * sums[c][ib]

@@ -436,6 +436,16 @@ __device__ __forceinline__ bool inside_poly(const SourceDev& s, float x, float y
 // Event of global photon index idx (binary search on the prefix sums) and
 // the photon's first state: direction and polarisation as for any source,
 // position from the event's point / segment / ball.
+// Emission delay of the scintillation time profile (Sec. 2.2, Table 2): a
+// mixture of two exponentials, from its own draw of the source step.
+__device__ __forceinline__ float emission_delay(const PropParams& p, uint64_t pid, const TimeProfile& tp)
+{
+    if (tp.tau_s == 0.0f && tp.tau_t == 0.0f) return 0.0f;
+    const U4 u = draw4(p.seed, pid, kSourceStep, 0xFFFFFFFFu);
+    const float tau = u.u0 < tp.f_s ? tp.tau_s : tp.tau_t;
+    return -tau * logf(u.u1);
+}
+
 __device__ Photon make_event_photon(const PropParams& p, uint64_t idx)
 {
     uint32_t lo = 0, hi = p.n_events;  // find e with prefix[e] <= idx < prefix[e+1]
@@ -447,7 +457,7 @@ __device__ Photon make_event_photon(const PropParams& p, uint64_t idx)
     Photon ph;
     ph.pid = ((uint64_t)lo << 32) | (uint64_t)(idx - __ldg(&p.ev_prefix[lo]));
     ph.medium = ev.medium;
-    ph.time = ev.t0;
+    ph.time = ev.t0 + emission_delay(p, ph.pid, ev.prof);
     ph.last = LXO_NO_HIT;
     ph.step = 0;
     const U4 u = draw4(p.seed, ph.pid, kSourceStep, 0);
@@ -483,7 +493,7 @@ __device__ Photon make_photon(const PropParams& p, uint64_t idx)
     Photon ph;
     ph.pid = p.base + idx;
     ph.medium = s.medium;
-    ph.time = s.t0;
+    ph.time = s.t0 + emission_delay(p, ph.pid, s.prof);
     ph.last = LXO_NO_HIT;
     ph.step = 0;
     if (s.kind == LXO_SRC_EXPLICIT) {
@@ -538,7 +548,8 @@ __device__ Photon make_photon(const PropParams& p, uint64_t idx)
     return ph;
 }
 
-__global__ void k_sample_source(const __grid_constant__ PropParams p, float* pos, float* dir, float* pol)
+__global__ void k_sample_source(const __grid_constant__ PropParams p, float* pos, float* dir, float* pol,
+                                float* time)
 {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n) return;
@@ -546,6 +557,7 @@ __global__ void k_sample_source(const __grid_constant__ PropParams p, float* pos
     pos[3 * i] = ph.pos.x; pos[3 * i + 1] = ph.pos.y; pos[3 * i + 2] = ph.pos.z;
     dir[3 * i] = ph.dir.x; dir[3 * i + 1] = ph.dir.y; dir[3 * i + 2] = ph.dir.z;
     pol[3 * i] = ph.pol.x; pol[3 * i + 1] = ph.pol.y; pol[3 * i + 2] = ph.pol.z;
+    if (time) time[i] = ph.time;
 }
 
 // ---------------------------------------------------------------------------
@@ -821,29 +833,57 @@ constexpr uint32_t kChunkDefault = 64;
 #define LXO_MIN_BLOCKS 5
 #endif
 
-// Tally of one photon's fate: shared-memory fate counters, global per-channel
-// counts and arrival-time histogram, optional per-photon record.
+// Adds `v` at `addr` once per group of lanes in `mask` that share `key`: the
+// group's lowest lane adds the group's sum (u32 counters).
+__device__ __forceinline__ void warp_add_u32(unsigned mask, unsigned long long key, uint32_t* addr, uint32_t v)
+{
+    const unsigned grp = __match_any_sync(mask, key);
+    const uint32_t sum = __reduce_add_sync(grp, v);
+    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(grp) - 1)) atomicAdd(addr, sum);
+}
+
+// Tallies of the photons that reached their fate, for the lanes in `act`
+// (all of them call this together): fate counters in shared memory and the
+// global per-channel counts and arrival-time histogram, each aggregated over
+// the lanes of the warp that hit the same counter; optional per-photon record
+// and adjoint sums per lane.
 template <bool kAdjoint>
 __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s_f, const Photon& ph, int fate,
-                                      int detail, const float* tl)
+                                      int detail, const float* tl, unsigned act)
 {
+    const uint32_t lane = threadIdx.x & 31u;
     // row of the per-channel tallies: the channel, or event * P + channel for batched events
     const size_t row = p.n_events ? (size_t)(ph.pid >> 32) * p.n_chan + detail : (size_t)detail;
     if (kAdjoint && fate == LXO_FATE_DETECTED)
         for (int k = 0; k < p.adj_k; ++k)
             atomicAdd(&p.out.adjoint[row * p.adj_k + k], (double)tl[k * kPropThreads]);
-    atomicAdd(&s_f[fate], 1ull);
-    atomicAdd(&s_f[7], (unsigned long long)ph.step);
-    if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
-    if (fate == LXO_FATE_SURF_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + p.n_mat + detail], 1ull);
-    if (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) {
-        atomicAdd(&p.out.lce[row], 1u);
-        if (fate == LXO_FATE_DETECTED) {
-            atomicAdd(&p.out.det[row], 1u);
+    // fate counters: one shared atomic per distinct fate in the warp, one for the step total
+    {
+        const unsigned grp = __match_any_sync(act, fate);
+        if (lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(&s_f[fate], (unsigned long long)__popc(grp));
+        const uint32_t steps = __reduce_add_sync(act, ph.step);
+        if (lane == (uint32_t)(__ffs(act) - 1)) atomicAdd(&s_f[7], (unsigned long long)steps);
+    }
+    const bool where = fate == LXO_FATE_BULK_ABS || fate == LXO_FATE_SURF_ABS;
+    const unsigned m_where = __ballot_sync(act, where);
+    if (where) {
+        const int slot = LXO_FATES_FIXED + (fate == LXO_FATE_BULK_ABS ? detail : p.n_mat + detail);
+        const unsigned grp = __match_any_sync(m_where, slot);
+        if (lane == (uint32_t)(__ffs(grp) - 1)) atomicAdd(&s_f[slot], (unsigned long long)__popc(grp));
+    }
+    const bool arrived = fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL;
+    const unsigned m_arr = __ballot_sync(act, arrived);
+    if (arrived) {
+        warp_add_u32(m_arr, row, &p.out.lce[row], 1u);
+        const bool det = fate == LXO_FATE_DETECTED;
+        const unsigned m_det = __ballot_sync(m_arr, det);
+        if (det) {
+            warp_add_u32(m_det, row, &p.out.det[row], 1u);
             if (p.out.hist) {
                 const float b = floorf(ph.time / p.tbin);
                 const uint32_t bin = (b >= (float)p.n_tbins || !(b >= 0.0f)) ? p.n_tbins : (uint32_t)b;
-                atomicAdd(&p.out.hist[row * (p.n_tbins + 1) + bin], 1u);
+                const size_t cell = row * (p.n_tbins + 1) + bin;
+                warp_add_u32(m_det, cell, &p.out.hist[cell], 1u);
             }
         }
     }
@@ -884,8 +924,9 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
         uint32_t need = __ballot_sync(FULL_MASK, !alive);
         const int idle = __popc(need);
         if (idle >= LXO_REFILL_MIN || idle == 32) {
+            const unsigned act = __ballot_sync(FULL_MASK, pending);
             if (pending) {
-                tally<kAdjoint>(p, s_f, ph, fate, detail, tl);
+                tally<kAdjoint>(p, s_f, ph, fate, detail, tl, act);
                 pending = false;
             }
             while (need && !exhausted) {
@@ -956,12 +997,13 @@ cudaError_t launch_trace(const Scene& sc, const float* org, const float* dir, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, cudaStream_t st)
+cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, float* time,
+                                 cudaStream_t st)
 {
     if (p.n == 0) return cudaSuccess;
     const int threads = 128;
     const uint64_t blocks = (p.n + threads - 1) / threads;
-    k_sample_source<<<(unsigned)blocks, threads, 0, st>>>(p, pos, dir, pol);
+    k_sample_source<<<(unsigned)blocks, threads, 0, st>>>(p, pos, dir, pol, time);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,24 @@ class Source:
     center: tuple = (0.0, 0.0, 0.0)   # POINT / BALL centre, SEGMENT start
     p1: tuple = (0.0, 0.0, 0.0)       # SEGMENT end
     t0: float = 0.0
+    # scintillation time profile: delay from the singlet component (tau_singlet)
+    # with probability singlet_frac, else the triplet one; both 0 = no delay
+    singlet_frac: float = 0.0
+    tau_singlet_ns: float = 0.0
+    tau_triplet_ns: float = 0.0
+
+    def with_profile(self, profile):
+        """This source with a scintillation time profile (singlet_frac,
+        tau_singlet_ns, tau_triplet_ns), e.g. NR_PROFILE."""
+        from dataclasses import replace
+        return replace(self, singlet_frac=profile[0], tau_singlet_ns=profile[1], tau_triplet_ns=profile[2])
+
+
+# Scintillation time profiles of LXe at 175 nm (Table 2 of the paper): singlet
+# fraction, singlet and triplet time constants in ns, for nuclear and
+# electronic recoils
+NR_PROFILE = (0.66, 3.5, 24.0)
+ER_PROFILE = (0.22, 3.5, 24.0)
 
 
 @dataclass
@@ -360,15 +378,16 @@ def hex_lattice(pitch, extent):
 # ----------------------------------------------------------------------------
 # detector parts
 # ----------------------------------------------------------------------------
-def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_plate, subdivide=False):
+def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_plate, subdivide=False, holes=True):
     """PTFE plate at ``z_plate`` filling the wall polygon, with a circular hole
     of radius ``r_window`` at every hex-lattice site whose window fits inside
-    the wall.  ``facing`` = +1 if the plate faces up (bottom array), -1 if it
-    faces down (top array).  Returns the PMT centres (x, y)."""
+    the wall (no holes if not ``holes``).  ``facing`` = +1 if the plate faces
+    up (bottom array), -1 if it faces down (top array).  Returns the PMT
+    centres (x, y)."""
     extent = np.abs(wall2).max() + pitch
     centres = hex_lattice(pitch, extent)
     # a PMT sits on every site whose window circle is inside the wall (0.5 mm clearance)
-    has_pmt = _inside_convex(centres, wall2, margin=r_window + 0.5)
+    has_pmt = _inside_convex(centres, wall2, margin=r_window + 0.5) & holes
     hexagon = polygon_vertices(6, pitch / math.sqrt(3), math.pi / 6)  # flat-to-flat = pitch
     pmts, cells = [], []
     normal = (0.0, 0.0, -float(facing))  # plate normal points from Xe into PTFE
@@ -579,7 +598,9 @@ def small_tpc(r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe
 
 def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "anode", "cathode"),
            r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe_ray_mm=400.0,
-           r_ss=0.30, ss_spec_frac=2.0 / 3.0, k_seg=32, active_only=True, window_rings=2, plate_subdivide=False):
+           r_ss=0.30, ss_spec_frac=2.0 / 3.0, k_seg=32, active_only=True, window_rings=2, plate_subdivide=False,
+           ptfe_spec_frac=0.0, coated=(), r_coat=0.90, coat_spec_frac=0.85 / 0.90, single_phase=False,
+           bottom_array=True, r_ptfe_bottom=0.99, gxe_abs_mm=1e9, gxe_ray_mm=INF):
     """DARWIN-scale dual-phase TPC (Sec. 2.1, Table 1): 24-sided PTFE wall
     inscribed in r = 1300 mm; gate z = 0 (LXe), liquid surface z = +2, anode
     z = +8 (GXe), cathode z = -2598; hex-packed 3-inch windows (76.2 mm, 5 mm
@@ -588,38 +609,69 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
     +69 / -2693; electrodes as hexagonal stainless-steel wire meshes (square
     wires of ``wire_um``, flat-to-flat ``mesh_pitch``) with R = 0.30 and
     specular/diffuse ratio 2 (Table 2).  Source: uniform in the active LXe,
-    z in [-2597, -1] (Sec. 3, average-LCE definition), isotropic."""
+    z in [-2597, -1] (Sec. 3, average-LCE definition), isotropic.
+
+    Design variants (Sec. 5):
+    * ``coated``: names of electrodes whose wires carry an Al/MgF2 coating,
+      total reflectivity ``r_coat`` of which ``coat_spec_frac`` specular
+      (Sec. 5.1: 90 %, 85 of it specular);
+    * ``single_phase``: LXe fills the detector up to the top array, with no
+      liquid surface (Sec. 5.3); the PTFE above the gate then has the LXe
+      reflectivity;
+    * ``bottom_array=False``: the bottom array is replaced by a PTFE plate of
+      reflectivity ``r_ptfe_bottom`` (Sec. 5.4: 99 %);
+    * ``ptfe_spec_frac``: specular fraction of the PTFE reflection."""
     R = 1300.0
     z_bot, z_cath, z_gate, z_liq, z_anode, z_top = -2688.0, -2598.0, 0.0, 2.0, 8.0, 64.0
     r_w, r_pc, thick = 38.1, 32.0, 5.0
-    mats = default_materials(lxe_abs_mm, lxe_ray_mm)
+    mats = default_materials(lxe_abs_mm, lxe_ray_mm, gxe_abs_mm, gxe_ray_mm)
     S_PTFE_L, S_PTFE_G, S_CAP, S_PC = 0, 1, 2, 3
+    gas = LXE if single_phase else GXE
     surfs = [
-        Surface("PTFE_LXe", REFLECTOR, r_ptfe_lxe, 0.0),
-        Surface("PTFE_GXe", REFLECTOR, r_ptfe_gxe, 0.0),
+        Surface("PTFE_LXe", REFLECTOR, r_ptfe_lxe, ptfe_spec_frac),
+        Surface("PTFE_GXe", REFLECTOR, r_ptfe_lxe if single_phase else r_ptfe_gxe, ptfe_spec_frac),
         Surface("PMT_cap", ABSORBER),
         Surface("photocathode", PHOTOCATHODE, qe=qe),
     ]
+    s_bottom = S_PTFE_L
+    if not bottom_array:
+        s_bottom = len(surfs)
+        surfs.append(Surface("PTFE_bottom", REFLECTOR, r_ptfe_bottom, ptfe_spec_frac))
     wall2 = polygon_vertices(24, R)
     b = _Builder()
-    bot, bot_edge = _pmt_plate(b, wall2, z_bot, pitch_pmt, r_w, k_seg, +1, LXE, S_PTFE_L, plate_subdivide)
-    top, top_edge = _pmt_plate(b, wall2, z_top, pitch_pmt, r_w, k_seg, -1, GXE, S_PTFE_G, plate_subdivide)
+    bot, bot_edge = _pmt_plate(b, wall2, z_bot, pitch_pmt, r_w, k_seg, +1, LXE, s_bottom, plate_subdivide,
+                               holes=bottom_array)
+    top, top_edge = _pmt_plate(b, wall2, z_top, pitch_pmt, r_w, k_seg, -1, gas, S_PTFE_G, plate_subdivide)
     _wall(b, wall2, z_bot, z_liq, LXE, S_PTFE_L, bottom_pts=bot_edge)
-    _wall(b, wall2, z_liq, z_top, GXE, S_PTFE_G, top_pts=top_edge)
-    b.add(_fan(wall2, z_liq, (0, 0)), (0, 0, 1), LXE, GXE)
+    _wall(b, wall2, z_liq, z_top, gas, S_PTFE_G, top_pts=top_edge)
+    if not single_phase:
+        b.add(_fan(wall2, z_liq, (0, 0)), (0, 0, 1), LXE, GXE)
     _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_pc, k_seg, LXE, S_CAP, S_PC, 0, rings=window_rings)
-    _pmt_windows(b, top, z_top, thick, -1, r_w, r_pc, k_seg, GXE, S_CAP, S_PC, len(bot), rings=window_rings)
-    zs = dict(gate=(z_gate, LXE), anode=(z_anode, GXE), cathode=(z_cath, LXE))
+    _pmt_windows(b, top, z_top, thick, -1, r_w, r_pc, k_seg, gas, S_CAP, S_PC, len(bot), rings=window_rings)
+    zs = dict(gate=(z_gate, LXE), anode=(z_anode, gas), cathode=(z_cath, LXE))
     for name in electrodes:
         ze, mat = zs[name]
         sid = len(surfs)
-        surfs.append(Surface(f"{name}_SS", REFLECTOR, r_ss, ss_spec_frac))
+        if name in coated:
+            surfs.append(Surface(f"{name}_AlMgF2", REFLECTOR, r_coat, coat_spec_frac))
+        else:
+            surfs.append(Surface(f"{name}_SS", REFLECTOR, r_ss, ss_spec_frac))
         v, t = hex_wire_mesh(wall2, ze, mesh_pitch, wire_um * 1e-3)
         b.add_indexed(v, t, OPAQUE, mat, sid)
     z0, z1 = (z_cath + 1.0, z_gate - 1.0) if active_only else (z_bot, z_liq)
     src = Source(SRC_VOLUME_POLYGON, LXE, n_sides=24, radius=R, z_min=z0, z_max=z1)
     return _detector("darwin", b, mats, surfs, bot, top, z_bot - thick, z_top + thick, src,
-                     dict(radius=R, wall_sides=24, z_liquid=z_liq, electrodes=list(electrodes)))
+                     dict(radius=R, wall_sides=24, z_liquid=None if single_phase else z_liq,
+                          electrodes=list(electrodes), coated=list(coated), single_phase=single_phase,
+                          bottom_array=bottom_array))
+
+
+# Best-guess optical constants of the paper's Table 2 (the workloads above use
+# the benchmark optics instead): L_Rayleigh 36 cm in LXe, 500 m absorption and
+# 200 m Rayleigh length in GXe, PTFE 99 % in LXe and 80 % in GXe with a
+# specular/diffuse ratio of 0.05 (specular fraction 0.05 / 1.05).
+PAPER_OPTICS = dict(lxe_abs_mm=50_000.0, lxe_ray_mm=360.0, gxe_abs_mm=500_000.0, gxe_ray_mm=200_000.0,
+                    r_ptfe_lxe=0.99, r_ptfe_gxe=0.80, ptfe_spec_frac=0.05 / 1.05)
 
 
 def _detector(name, b, mats, surfs, bot, top, z_pc_bot, z_pc_top, src, info):

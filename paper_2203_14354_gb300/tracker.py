@@ -36,6 +36,8 @@ def make_source(src: Source, explicit=None) -> A.lxo_source:
     s.center[:] = [float(x) for x in src.center]
     s.p1[:] = [float(x) for x in src.p1]
     s.t0 = float(src.t0)
+    s.singlet_frac, s.tau_singlet_ns, s.tau_triplet_ns = (float(src.singlet_frac), float(src.tau_singlet_ns),
+                                                          float(src.tau_triplet_ns))
     if explicit is not None:
         pos, dir, pol = explicit
         s.pos, s.dir, s.pol = pos.data_ptr(), dir.data_ptr(), pol.data_ptr()
@@ -192,14 +194,16 @@ class Tracker:
                                            _ptr(t), _stream(stream)))
         return hit, t
 
-    def sample_source(self, n, base=0, seed=0, source=None, stream=None):
+    def sample_source(self, n, base=0, seed=0, source=None, stream=None, time=False):
+        """First photon states (pos, dir, pol [n, 3]; and emission times [n] if time)."""
         src = make_source(source or self.det.source)
         pos = torch.empty((n, 3), dtype=torch.float32, device=self.device)
         dir = torch.empty_like(pos)
         pol = torch.empty_like(pos)
+        t = torch.empty(n, dtype=torch.float32, device=self.device) if time else None
         self._check(self._L.lxo_sample_source(self._ctx, C.byref(src), n, base, seed, _ptr(pos), _ptr(dir), _ptr(pol),
-                                              _stream(stream)))
-        return pos, dir, pol
+                                              _ptr(t), _stream(stream)))
+        return (pos, dir, pol, t) if time else (pos, dir, pol)
 
     # -- propagation --------------------------------------------------------
     def alloc_results(self, n_tbins=1000, per_photon_n=0):
@@ -280,6 +284,8 @@ class Tracker:
             e.center[:] = [float(x) for x in src.center]
             e.p1[:] = [float(x) for x in src.p1]
             e.radius, e.t0, e.n_photons = float(src.radius), float(src.t0), int(n)
+            e.singlet_frac, e.tau_singlet_ns, e.tau_triplet_ns = (float(src.singlet_frac), float(src.tau_singlet_ns),
+                                                                  float(src.tau_triplet_ns))
         self._check(self._L.lxo_upload_events(self._ctx, arr, len(events)))
         self.n_events = len(events)
         self.event_photons = int(sum(int(n) for _, n in events))

@@ -1,0 +1,100 @@
+"""Design variants of the DARWIN-scale detector (Sec. 5 of the paper) as
+geometry and surface switches, each propagated on the GPU: light-collection
+efficiency (photons reaching a photocathode, Sec. 3) in total and per array,
+and t90 with the nuclear-recoil scintillation profile.
+
+The paper's printed results are reported beside each variant as context: its
+geometry came from CAD (five electrodes of parallel wires, frames, PTFE
+around the PMTs), this one is procedural (three hexagonal meshes, flat
+plates), so absolute values differ; the direction and rough size of each
+change are the comparison.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+
+from . import analysis
+from . import geometry as g
+
+# Sec. 5 results at L_abs = 50 m, best-guess optics (LCE %, top, bottom; t90 ns)
+PAPER = {
+    "baseline": dict(lce=43.1, top=14.8, bottom=28.2, t90=200.0),
+    "gate_coated": dict(lce=46.0, top=16.8, bottom=29.2),
+    "all_coated": dict(lce=51.8, top=18.6, bottom=33.2),
+    "single_phase": dict(lce_change_abs=4.9, t90=175.0),
+    "no_bottom_array": dict(lce=18.0, t90=265.0),
+    "baseline_abs500m": dict(lce=54.0, top=18.7, bottom=35.3),
+    "all_coated_abs500m": dict(lce=67.0, top=24.3, bottom=42.7, t90=240.0),
+}
+
+
+def measure(trk, det, n, seed=0):
+    """LCE (total, top, bottom) of n photons uniform in the active LXe, and
+    t90 (ns) of the detected photons with the nuclear-recoil profile."""
+    out = trk.propagate(n, seed=seed, source=det.source.with_profile(g.NR_PROFILE), n_tbins=1000, tbin_ns=1.0)
+    lce = out["lce"].cpu().numpy().astype(np.float64)
+    top = det.pmt_array == 1
+    return dict(lce=100.0 * lce.sum() / n, top=100.0 * lce[top].sum() / n, bottom=100.0 * lce[~top].sum() / n,
+                t90=analysis.t90(out["hist"].cpu().numpy(), 1.0),
+                escaped=int(out["fates"][4]), geom_err=int(out["fates"][6]))
+
+
+def coated_table(surfaces, coated, r_coat=0.90, coat_spec_frac=0.85 / 0.90):
+    """The surface table with the stainless-steel surfaces of the electrodes
+    named in `coated` replaced by an Al/MgF2 coating (Sec. 5.1)."""
+    out = []
+    for sf in surfaces:
+        el = sf.name[:-3] if sf.name.endswith("_SS") else None
+        out.append(g.Surface(f"{el}_AlMgF2", g.REFLECTOR, r_coat, coat_spec_frac) if el in coated else sf)
+    return out
+
+
+def run(n=10_000_000, electrodes=("gate", "anode", "cathode"), log=print):
+    from .tracker import Tracker
+
+    res = {}
+    el = tuple(electrodes)
+    t0 = time.perf_counter()
+    det = g.darwin(electrodes=el, **g.PAPER_OPTICS)
+    trk = Tracker(det)
+    log(f"baseline mesh: {det.n_tris} triangles, {time.perf_counter() - t0:.0f} s")
+    base_surfs = list(det.surfaces)
+    opt = g.PAPER_OPTICS
+    # coatings and the absorption length change only the tables of the same mesh
+    for name, coated, abs_mm in (("baseline", (), 50_000.0), ("gate_coated", ("gate",), 50_000.0),
+                                 ("all_coated", el, 50_000.0), ("baseline_abs500m", (), 500_000.0),
+                                 ("all_coated_abs500m", el, 500_000.0)):
+        det.surfaces = coated_table(base_surfs, coated)
+        det.materials = g.default_materials(abs_mm, opt["lxe_ray_mm"], opt["gxe_abs_mm"], opt["gxe_ray_mm"])
+        trk.set_surfaces(det.surfaces)
+        trk.set_materials(det.materials)
+        res[name] = measure(trk, det, n)
+        log(f"{name}: {res[name]}")
+    trk.close()
+    for name, kw in (("single_phase", dict(single_phase=True)), ("no_bottom_array", dict(bottom_array=False))):
+        d = g.darwin(electrodes=el, **opt, **kw)
+        t = Tracker(d)
+        res[name] = measure(t, d, n)
+        t.close()
+        log(f"{name}: {res[name]}")
+    res["single_phase"]["lce_change_abs"] = res["single_phase"]["lce"] - res["baseline"]["lce"]
+    return res
+
+
+def main(argv=None):
+    import argparse
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--photons", type=float, default=1e7)
+    a = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    res = run(int(a.photons), log=lambda s: print(s, flush=True))
+    print(json.dumps(dict(photons=int(a.photons), optics="paper best guess (Table 2)", ours=res, paper=PAPER,
+                          seconds=time.perf_counter() - t0)))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,63 @@
+"""Design variants of the DARWIN-scale detector (Sec. 5) as geometry and
+surface switches, checked on the mesh without the electrode wire meshes
+(the switches do not touch them): single phase has no gas and no liquid
+surface, the variant without a bottom array has only the top channels and a
+99 % PTFE floor, coatings change only the electrodes' surface entries, and
+the best-guess optics follow Table 2."""
+import numpy as np
+import pytest
+
+from paper_2203_14354_gb300 import geometry as g
+from paper_2203_14354_gb300 import variants
+
+
+@pytest.fixture(scope="module")
+def base():
+    return g.darwin(electrodes=())
+
+
+def test_single_phase(base):
+    d = g.darwin(electrodes=(), single_phase=True)
+    assert not np.any(d.mat_inner == g.GXE) and not np.any(d.mat_outer == g.GXE)
+    assert np.any(base.mat_outer == g.GXE)
+    # the liquid surface is gone: no LXe/GXe boundary, and nothing else changed in size
+    liquid = (base.mat_inner == g.LXE) & (base.mat_outer == g.GXE) & (base.surface == g.SURF_NONE)
+    assert liquid.sum() > 0 and d.n_tris == base.n_tris - liquid.sum()
+    assert d.surfaces[1].reflectivity == d.surfaces[0].reflectivity
+    assert d.n_pmts == base.n_pmts
+
+
+def test_no_bottom_array(base):
+    d = g.darwin(electrodes=(), bottom_array=False)
+    assert d.n_pmts == int((base.pmt_array == 1).sum()) and np.all(d.pmt_array == 1)
+    ch = d.channel[d.channel >= 0]
+    assert ch.min() == 0 and ch.max() == d.n_pmts - 1
+    floor = d.surfaces.index(next(s for s in d.surfaces if s.name == "PTFE_bottom"))
+    assert d.surfaces[floor].reflectivity == 0.99
+    z = d.verts[d.tris].mean(1)[:, 2]
+    at_floor = np.abs(z - (-2688.0)) < 1e-3
+    assert at_floor.sum() > 0 and np.all(d.surface[at_floor] == floor)
+
+
+def test_coatings_change_only_surfaces():
+    opt = dict(k_seg=8, pitch_pmt=400.0, mesh_pitch=200.0)
+    a = g.darwin(**opt)
+    b = g.darwin(coated=("gate",), **opt)
+    assert np.array_equal(a.tris, b.tris) and np.array_equal(a.surface, b.surface)
+    names = [s.name for s in b.surfaces]
+    assert "gate_AlMgF2" in names and "anode_SS" in names
+    gate = b.surfaces[names.index("gate_AlMgF2")]
+    assert gate.reflectivity == 0.90 and gate.spec_frac == pytest.approx(0.85 / 0.90)
+    t = variants.coated_table(a.surfaces, ("gate", "anode", "cathode"))
+    assert [s.name for s in t if s.name.endswith("_AlMgF2")] == ["gate_AlMgF2", "anode_AlMgF2", "cathode_AlMgF2"]
+    assert [s.name for s in t][:4] == [s.name for s in a.surfaces][:4]
+
+
+def test_paper_optics():
+    d = g.darwin(electrodes=(), **g.PAPER_OPTICS)
+    lxe, gxe = d.materials[g.LXE], d.materials[g.GXE]
+    assert (lxe.abs_len_mm, lxe.rayleigh_len_mm) == (50_000.0, 360.0)
+    assert (gxe.abs_len_mm, gxe.rayleigh_len_mm) == (500_000.0, 200_000.0)
+    assert d.surfaces[0].reflectivity == 0.99 and d.surfaces[1].reflectivity == 0.80
+    # specular/diffuse ratio 0.05 -> specular fraction 0.05 / 1.05
+    assert d.surfaces[0].spec_frac / (1 - d.surfaces[0].spec_frac) == pytest.approx(0.05)
