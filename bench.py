@@ -35,10 +35,11 @@ METRIC = "photons/sec to fate, DARWIN mesh, 1 GB300"
 UNIT = "photons/s"
 OPS_PER_NODE, OPS_PER_TRI, OPS_PHYSICS = 40, 50, 250
 N_SM, LANES_PER_SM = 152, 128
-# DRAM bytes (read + write) per photon of the propagation kernel, from the ncu
-# capture summarised in profiles/ (None while the kernel differs from the one
-# captured)
-DRAM_BYTES_PER_PHOTON = 2352  # profiles/k_propagate_darwin.md (2e6-photon capture, scaled per photon)
+# DRAM bytes (read + write) per photon of the propagation kernel: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of one timed launch on 2e6
+# photons of this workload (4.622 GB + 0.163 GB), divided by 2e6; scales with
+# the photon count.  None while the kernel differs from the one captured.
+DRAM_BYTES_PER_PHOTON = 2393
 
 
 def parse():
