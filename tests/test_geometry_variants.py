@@ -61,3 +61,21 @@ def test_paper_optics():
     assert d.surfaces[0].reflectivity == 0.99 and d.surfaces[1].reflectivity == 0.80
     # specular/diffuse ratio 0.05 -> specular fraction 0.05 / 1.05
     assert d.surfaces[0].spec_frac / (1 - d.surfaces[0].spec_frac) == pytest.approx(0.05)
+
+
+def _edge_uses(det):
+    t = det.tris
+    e = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]]).astype(np.int64), 1)
+    return np.unique(e, axis=0, return_counts=True)[1]
+
+
+@pytest.mark.parametrize("build", [g.small_tpc, g.scaled_tpc,
+                                   lambda: g.darwin(electrodes=()),
+                                   lambda: g.darwin(electrodes=(), single_phase=True),
+                                   lambda: g.darwin(electrodes=(), bottom_array=False)])
+def test_surfaces_have_no_open_edges(build):
+    """Conforming meshes (no T-junctions): every edge belongs to two
+    triangles, or three where a plate, a window rim or the liquid surface
+    meets another surface; none is open, so no photon leaks through a gap."""
+    uses = _edge_uses(build())
+    assert uses.min() >= 2 and uses.max() <= 3
