@@ -40,6 +40,11 @@ N_SM, LANES_PER_SM = 152, 128
 # photons of this workload (4.622 GB + 0.163 GB), divided by 2e6; scales with
 # the photon count.  None while the kernel differs from the one captured.
 DRAM_BYTES_PER_PHOTON = 2393
+# warp instructions issued per photon step by the same capture
+# (smsp__inst_executed.sum 1.266e10 over 5.15e7 steps); the issue-slot peak is
+# 152 SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
+WARP_INST_PER_STEP = 245.0
+SCHEDULERS_PER_SM = 4
 
 
 def parse():
@@ -343,6 +348,8 @@ def main():
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     alu_peak = N_SM * LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    issue_rate = steps_total * WARP_INST_PER_STEP / kern_s
+    issue_peak = N_SM * SCHEDULERS_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
 
     # end to end through the C ABI with host result buffers (copies in the timed region)
     e2e_steps = max(1, min(args.steps, 3))
@@ -394,7 +401,11 @@ def main():
                                       "fetch_bytes": bytes_per_step},
                          "fetch": {"achieved_gbs": fetch_gbs, "hbm_peak_gbs": hbm, "frac_of_hbm": fetch_gbs / hbm},
                          "steps_per_photon": steps_total / n, "kernel_ms": statistics.mean(kern_ms),
-                         "simd_efficiency": simd},
+                         "simd_efficiency": simd,
+                         "issue": {"warp_inst_per_step": WARP_INST_PER_STEP,
+                                   "achieved_g_warp_inst_s": issue_rate / 1e9,
+                                   "peak_g_warp_inst_s": issue_peak / 1e9, "frac": issue_rate / issue_peak,
+                                   "source": "warp instructions per step from the ncu capture of this kernel"}},
             "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * 1,
