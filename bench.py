@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward+adjoint cost measurement")
+    ap.add_argument("--no-adjoint-fd", action="store_true",
+                    help="skip the 1e9-photon finite-difference check of the adjoint")
     ap.add_argument("--no-events", action="store_true", help="skip the batched-events measurement")
     return ap.parse_args()
 
@@ -177,9 +179,85 @@ def adjoint_cost(args, n=10_000_000, reps=3):
             ts.append(a.elapsed_time(b))
         times[adj] = statistics.median(ts)
     trk.sync()
-    return {"workload": "50 cm dual-phase TPC, 61+61 PMTs, thin-disk gate/anode/cathode, 1e7 photons, 7 parameters",
-            "fwd_ms": times[False], "fwd_adjoint_ms": times[True], "ratio": times[True] / times[False],
-            "fwd_photons_per_s": n / (times[False] / 1e3)}
+    res = {"workload": "50 cm dual-phase TPC, 61+61 PMTs, thin-disk gate/anode/cathode, 1e7 photons, 7 parameters",
+           "fwd_ms": times[False], "fwd_adjoint_ms": times[True], "ratio": times[True] / times[False],
+           "fwd_photons_per_s": n / (times[False] / 1e3)}
+    if not args.no_adjoint_fd:
+        res["fd_check"] = adjoint_fd_check(trk)
+    return res
+
+
+def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wide=3e-2, noisy=0.02):
+    """Accuracy of the adjoint gradient of detected hits (total, top array,
+    bottom array) against central finite differences with common random
+    numbers at relative step h (same seed and photon ids at theta +- h), 1e9
+    photons in 10 batches; mean and batch-means standard error of both
+    estimates per parameter and aggregate.  Parameters whose differences are
+    noisier than `noisy` (relative standard error) at h are differenced again
+    at h_wide: the noise of a common-random-number difference falls as
+    h^-1/2, its truncation error grows as h^2."""
+    top = torch_bool(trk.det.pmt_array == 1, trk.device)
+    theta0 = trk.theta()
+    aggs = ("total", "top", "bottom")
+
+    def sums(v):  # [P] or [P, Q] -> per aggregate
+        return [v.sum(0), v[top].sum(0), v[~top].sum(0)]
+
+    adj = np.zeros((len(aggs), batches, trk.n_params))
+    fd = np.zeros((len(aggs), batches, trk.n_params))
+    t0 = time.perf_counter()
+    trk.set_theta(theta0)
+    for b in range(batches):
+        out = trk.propagate(n_batch, base=b * n_batch, seed=seed, adjoint=True, n_tbins=1)
+        J = trk.jacobian(out["adjoint"])
+        for a, v in enumerate(sums(J)):
+            adj[a, b] = v.cpu().numpy()
+    def differences(q, hq, dst):
+        step = hq * float(theta0[q])
+        for b in range(batches):
+            res = []
+            for sgn in (1.0, -1.0):
+                th = theta0.clone()
+                th[q] += sgn * step
+                trk.set_theta(th)
+                det = trk.propagate(n_batch, base=b * n_batch, seed=seed, n_tbins=1)["det"].double()
+                res.append([float(x) for x in sums(det)])
+            for a in range(len(aggs)):
+                dst[a, b, q] = (res[0][a] - res[1][a]) / (2.0 * step)
+
+    for q in range(trk.n_params):
+        differences(q, h, fd)
+    fd_w = np.full_like(fd, np.nan)
+    wide = [q for q in range(trk.n_params)
+            if np.max(fd[:, :, q].std(1, ddof=1) / math.sqrt(batches) / np.abs(fd[:, :, q].mean(1))) > noisy]
+    for q in wide:
+        differences(q, h_wide, fd_w)
+    trk.set_theta(theta0)
+    names = ["L_abs_LXe", "L_ray_LXe", "R_PTFE_LXe", "R_PTFE_GXe", "T_gate", "T_anode", "T_cathode"]
+    out = {"photons": batches * n_batch, "h_rel": h, "params": names[:trk.n_params],
+           "seconds": time.perf_counter() - t0}
+    def compare(a, d):
+        a_m, f_m = adj[a].mean(0), d[a].mean(0)
+        a_s = adj[a].std(0, ddof=1) / math.sqrt(batches)
+        f_s = d[a].std(0, ddof=1) / math.sqrt(batches)
+        return {"adjoint": a_m.tolist(), "adjoint_se": a_s.tolist(), "fd": f_m.tolist(), "fd_se": f_s.tolist(),
+                "rel_diff": (np.abs(a_m - f_m) / np.abs(f_m)).tolist(),
+                "z": (np.abs(a_m - f_m) / np.sqrt(a_s ** 2 + f_s ** 2)).tolist()}
+
+    for a, name in enumerate(aggs):
+        out[name] = compare(a, fd)
+    if wide:
+        out["wide_step"] = {"h_rel": h_wide, "params": [names[q] for q in wide]}
+        for a, name in enumerate(aggs):
+            c = compare(a, fd_w)
+            out["wide_step"][name] = {k: [v[q] for q in wide] for k, v in c.items()}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def torch_bool(mask, device):
+    import torch
+    return torch.from_numpy(np.asarray(mask, bool)).to(device)
 
 
 def events_throughput(det, reps=3):
