@@ -205,28 +205,35 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
 
     adj = np.zeros((len(aggs), batches, trk.n_params))
     fd = np.zeros((len(aggs), batches, trk.n_params))
+    P = trk.n_channels
+    adj_pmt = np.zeros((batches, P, trk.n_params))
+    fd_pmt = np.zeros((batches, P, trk.n_params))
     t0 = time.perf_counter()
     trk.set_theta(theta0)
     for b in range(batches):
         out = trk.propagate(n_batch, base=b * n_batch, seed=seed, adjoint=True, n_tbins=1)
         J = trk.jacobian(out["adjoint"])
+        adj_pmt[b] = J.cpu().numpy()
         for a, v in enumerate(sums(J)):
             adj[a, b] = v.cpu().numpy()
-    def differences(q, hq, dst):
+    def differences(q, hq, dst, per_pmt=None):
         step = hq * float(theta0[q])
         for b in range(batches):
-            res = []
+            res, dets = [], []
             for sgn in (1.0, -1.0):
                 th = theta0.clone()
                 th[q] += sgn * step
                 trk.set_theta(th)
                 det = trk.propagate(n_batch, base=b * n_batch, seed=seed, n_tbins=1)["det"].double()
                 res.append([float(x) for x in sums(det)])
+                dets.append(det.cpu().numpy())
             for a in range(len(aggs)):
                 dst[a, b, q] = (res[0][a] - res[1][a]) / (2.0 * step)
+            if per_pmt is not None:
+                per_pmt[b, :, q] = (dets[0] - dets[1]) / (2.0 * step)
 
     for q in range(trk.n_params):
-        differences(q, h, fd)
+        differences(q, h, fd, fd_pmt)
     fd_w = np.full_like(fd, np.nan)
     wide = [q for q in range(trk.n_params)
             if np.max(fd[:, :, q].std(1, ddof=1) / math.sqrt(batches) / np.abs(fd[:, :, q].mean(1))) > noisy]
@@ -246,6 +253,25 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
 
     for a, name in enumerate(aggs):
         out[name] = compare(a, fd)
+    # per PMT: paired batch differences adjoint - FD (same photons in a
+    # batch), t_c = mean / standard error with nu = batches - 1; under
+    # agreement sum_c t_c^2 has mean n nu / (nu - 2) and variance
+    # n 2 nu^2 (nu - 1) / ((nu - 2)^2 (nu - 4))
+    e = adj_pmt - fd_pmt
+    se = e.std(0, ddof=1) / math.sqrt(batches)
+    nu = batches - 1
+    sum_t2, n_pmt, z_sum = [], [], []
+    for q in range(trk.n_params):
+        ok = se[:, q] > 0
+        t2 = (e.mean(0)[ok, q] / se[ok, q]) ** 2
+        n = int(ok.sum())
+        mean = n * nu / (nu - 2)
+        sd = math.sqrt(n * 2 * nu ** 2 * (nu - 1) / ((nu - 2) ** 2 * (nu - 4)))
+        sum_t2.append(float(t2.sum()))
+        n_pmt.append(n)
+        z_sum.append(float((t2.sum() - mean) / sd) if n else None)
+    out["per_pmt"] = {"sum_t2": sum_t2, "pmts": n_pmt, "expected": [k * nu / (nu - 2) for k in n_pmt],
+                      "z": z_sum}
     if wide:
         out["wide_step"] = {"h_rel": h_wide, "params": [names[q] for q in wide]}
         for a, name in enumerate(aggs):
