@@ -550,6 +550,95 @@ def hex_wire_mesh(wall2, z, pitch, wire, margin=1.0):
     return verts, tris
 
 
+def parallel_wires(wall2, z, pitch, wire, r_end, along=0):
+    """Plane of parallel wires (Sec. 2.1: stainless-steel wires of 200 um at
+    5 or 7.5 mm pitch) running along x (along=0) or y (1) at height z,
+    square-section prisms of width ``wire`` (8 triangles each, same
+    construction as the hex meshes), each cut where it leaves the polygon
+    wall2 scaled to circumradius ``r_end`` (the wire ends lie inside the
+    frame).  Returns (verts [m,3], tris [k,3]), outward-facing."""
+    R = float(np.abs(wall2).max())
+    inner = wall2 * (r_end / R)
+    offs = np.arange(-math.floor(r_end / pitch), math.floor(r_end / pitch) + 1) * pitch
+    h = wire / 2.0
+    verts, tris = [], []
+    for o in offs:
+        # chord of the inner polygon along the wire direction at offset o
+        p = np.array([[-2 * R, o], [2 * R, o]]) if along == 0 else np.array([[o, -2 * R], [o, 2 * R]])
+        seg = _clip_segment(p[0], p[1], inner)
+        if seg is None or np.linalg.norm(seg[1] - seg[0]) < 10 * wire:
+            continue
+        P0, P1 = seg
+        u = (P1 - P0) / np.linalg.norm(P1 - P0)
+        v = np.array([-u[1], u[0]])
+        cs = np.array([[1, 1], [-1, 1], [-1, -1], [1, -1]], np.float64) * h
+        vv = np.zeros((8, 3))
+        for k in range(4):
+            for e, P in enumerate((P0, P1)):
+                vv[4 * e + k, :2] = P + cs[k, 0] * v
+                vv[4 * e + k, 2] = z + cs[k, 1]
+        t = []
+        for k in range(4):
+            k1 = (k + 1) % 4
+            t += [(k, k1, 4 + k1), (k, 4 + k1, 4 + k)]
+        t = np.array(t, np.int64)
+        tv = vv[t]
+        nrm = np.cross(tv[:, 1] - tv[:, 0], tv[:, 2] - tv[:, 0])
+        mid = np.array([*(P0 + P1) / 2, z])
+        flip = (nrm * (tv.mean(1) - mid)).sum(1) < 0
+        t[flip] = t[flip][:, [0, 2, 1]]
+        tris.append(t + 8 * len(verts))
+        verts.append(vv)
+    if not verts:
+        return np.zeros((0, 3)), np.zeros((0, 3), np.int64)
+    return np.concatenate(verts), np.concatenate(tris)
+
+
+def _clip_segment(a, b, poly):
+    """Part of segment a-b inside the convex polygon (counter-clockwise), or None."""
+    t0, t1 = 0.0, 1.0
+    d = b - a
+    n = poly.shape[0]
+    for k in range(n):
+        p, q = poly[k], poly[(k + 1) % n]
+        e = q - p
+        nrm = np.array([e[1], -e[0]])  # outward for a counter-clockwise polygon
+        den = nrm @ d
+        num = nrm @ (p - a)
+        if abs(den) < 1e-15:
+            if num < 0:
+                return None
+            continue
+        t = num / den
+        if den > 0:
+            t1 = min(t1, t)
+        else:
+            t0 = max(t0, t)
+        if t0 > t1:
+            return None
+    return a + t0 * d, a + t1 * d
+
+
+def _frame(b, wall2, z_lo, z_hi, r_in, mat_xe, surf):
+    """Electrode frame (Sec. 2.1: an extruded 24-sided polygon on which the
+    wires are fixed): the annulus between the wall polygon and the polygon
+    scaled to circumradius r_in, from z_lo to z_hi, opaque inside; its outer
+    face is the wall itself."""
+    R = float(np.abs(wall2).max())
+    inner = wall2 * (r_in / R)
+    c = (0.0, 0.0)
+    b.add(_ring(wall2, inner, z_hi, c), (0, 0, -1), mat_xe, OPAQUE, surf)   # top face, normal into the frame
+    b.add(_ring(wall2, inner, z_lo, c), (0, 0, 1), mat_xe, OPAQUE, surf)    # bottom face
+    n = inner.shape[0]
+    i0 = np.concatenate([inner, np.full((n, 1), z_lo)], 1)
+    i1 = np.concatenate([inner, np.full((n, 1), z_hi)], 1)
+    i0n, i1n = np.roll(i0, -1, 0), np.roll(i1, -1, 0)
+    side = np.concatenate([np.stack([i0, i0n, i1n], 1), np.stack([i0, i1n, i1], 1)])
+    nrm = side.mean(1)
+    nrm[:, 2] = 0.0
+    b.add(side, nrm, mat_xe, OPAQUE, surf)  # inner face, normal radially outwards = into the frame
+
+
 # ----------------------------------------------------------------------------
 # optical tables (Table 2 of the paper; workload values override it)
 # ----------------------------------------------------------------------------
@@ -600,7 +689,7 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
            r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe_ray_mm=400.0,
            r_ss=0.30, ss_spec_frac=2.0 / 3.0, k_seg=32, active_only=True, window_rings=2, plate_subdivide=False,
            ptfe_spec_frac=0.0, coated=(), r_coat=0.90, coat_spec_frac=0.85 / 0.90, single_phase=False,
-           bottom_array=True, r_ptfe_bottom=0.99, gxe_abs_mm=1e9, gxe_ray_mm=INF):
+           bottom_array=True, r_ptfe_bottom=0.99, gxe_abs_mm=1e9, gxe_ray_mm=INF, electrode_kind="mesh"):
     """DARWIN-scale dual-phase TPC (Sec. 2.1, Table 1): 24-sided PTFE wall
     inscribed in r = 1300 mm; gate z = 0 (LXe), liquid surface z = +2, anode
     z = +8 (GXe), cathode z = -2598; hex-packed 3-inch windows (76.2 mm, 5 mm
@@ -620,7 +709,14 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
       reflectivity;
     * ``bottom_array=False``: the bottom array is replaced by a PTFE plate of
       reflectivity ``r_ptfe_bottom`` (Sec. 5.4: 99 %);
-    * ``ptfe_spec_frac``: specular fraction of the PTFE reflection."""
+    * ``ptfe_spec_frac``: specular fraction of the PTFE reflection;
+    * ``electrode_kind="wires"``: the paper's own baseline electrodes (Sec.
+      2.1, Table 1) instead of the hex meshes: five planes of parallel
+      200 um stainless-steel wires, top screen z = 54, anode z = 12 and gate
+      z = 0 at 5 mm pitch, cathode z = -2598 and bottom screen z = -2678 at
+      7.5 mm pitch, each fixed to a 24-gon frame 20 mm wide and 8 mm high
+      (PTFE-covered on top, bare steel below; a surface entry of its own);
+      ``electrodes`` is ignored."""
     R = 1300.0
     z_bot, z_cath, z_gate, z_liq, z_anode, z_top = -2688.0, -2598.0, 0.0, 2.0, 8.0, 64.0
     r_w, r_pc, thick = 38.1, 32.0, 5.0
@@ -648,8 +744,30 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
         b.add(_fan(wall2, z_liq, (0, 0)), (0, 0, 1), LXE, GXE)
     _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_pc, k_seg, LXE, S_CAP, S_PC, 0, rings=window_rings)
     _pmt_windows(b, top, z_top, thick, -1, r_w, r_pc, k_seg, gas, S_CAP, S_PC, len(bot), rings=window_rings)
+    if electrode_kind == "wires":
+        # (name, wire plane z, frame z range, xenon phase, pitch, frame surface)
+        planes = (("screen_top", 54.0, (50.0, 58.0), gas, 5.0, S_PTFE_G),
+                  ("anode", 12.0, (8.0, 16.0), gas, 5.0, S_PTFE_G),
+                  ("gate", 0.0, (-9.0, -1.0), LXE, 5.0, S_PTFE_L),
+                  ("cathode", -2598.0, (-2602.0, -2594.0), LXE, 7.5, None),
+                  ("screen_bottom", -2678.0, (-2682.0, -2674.0), LXE, 7.5, None))
+        # gate frame below the plane so that it stays in the liquid
+        for name, zw, (f0, f1), mat, pitch, fsurf in planes:
+            sid = len(surfs)
+            if name in coated:
+                surfs.append(Surface(f"{name}_AlMgF2", REFLECTOR, r_coat, coat_spec_frac))
+            else:
+                surfs.append(Surface(f"{name}_SS", REFLECTOR, r_ss, ss_spec_frac))
+            v, t = parallel_wires(wall2, zw, pitch, 0.200, r_end=R - 10.0)
+            b.add_indexed(v, t, OPAQUE, mat, sid)
+            # the frame: its own surface entry (PTFE-covered above, bare or coated steel below)
+            fid = len(surfs)
+            base = surfs[fsurf] if fsurf is not None else surfs[sid]
+            surfs.append(Surface(f"{name}_frame", REFLECTOR, base.reflectivity, base.spec_frac))
+            _frame(b, wall2, f0, f1, R - 20.0, mat, fid)
+        electrodes = tuple(p[0] for p in planes)
     zs = dict(gate=(z_gate, LXE), anode=(z_anode, gas), cathode=(z_cath, LXE))
-    for name in electrodes:
+    for name in (electrodes if electrode_kind == "mesh" else ()):
         ze, mat = zs[name]
         sid = len(surfs)
         if name in coated:

@@ -29,17 +29,24 @@ PAPER = {
     "baseline_abs500m": dict(lce=54.0, top=18.7, bottom=35.3),
     "all_coated_abs500m": dict(lce=67.0, top=24.3, bottom=42.7, t90=240.0),
 }
+# Sec. 4.2, sources of photon losses (% of photons, baseline)
+PAPER_LOSSES = dict(not_detected=56.9, LXe=22.7, electrodes=18.0, gate=7.7, cathode=3.1, screen_bottom=2.6,
+                    anode=1.7, screen_top=1.6, frames=1.3, pmt_caps=9.0, ptfe=7.2)
 
 
-def measure(trk, det, n, seed=0):
+def measure(trk, det, n, seed=0, losses=False):
     """LCE (total, top, bottom) of n photons uniform in the active LXe, and
-    t90 (ns) of the detected photons with the nuclear-recoil profile."""
+    t90 (ns) of the detected photons with the nuclear-recoil profile; with
+    losses, the loss table."""
     out = trk.propagate(n, seed=seed, source=det.source.with_profile(g.NR_PROFILE), n_tbins=1000, tbin_ns=1.0)
     lce = out["lce"].cpu().numpy().astype(np.float64)
     top = det.pmt_array == 1
-    return dict(lce=100.0 * lce.sum() / n, top=100.0 * lce[top].sum() / n, bottom=100.0 * lce[~top].sum() / n,
-                t90=analysis.t90(out["hist"].cpu().numpy(), 1.0),
-                escaped=int(out["fates"][4]), geom_err=int(out["fates"][6]))
+    res = dict(lce=100.0 * lce.sum() / n, top=100.0 * lce[top].sum() / n, bottom=100.0 * lce[~top].sum() / n,
+               t90=analysis.t90(out["hist"].cpu().numpy(), 1.0),
+               escaped=int(out["fates"][4]), geom_err=int(out["fates"][6]))
+    if losses:
+        res["losses"] = analysis.loss_table(det, out["fates"].cpu().numpy(), n)
+    return res
 
 
 def coated_table(surfaces, coated, r_coat=0.90, coat_spec_frac=0.85 / 0.90):
@@ -81,6 +88,16 @@ def run(n=10_000_000, electrodes=("gate", "anode", "cathode"), log=print):
         t.close()
         log(f"{name}: {res[name]}")
     res["single_phase"]["lce_change_abs"] = res["single_phase"]["lce"] - res["baseline"]["lce"]
+    # the paper's own electrodes: five planes of parallel wires on frames
+    d = g.darwin(electrode_kind="wires", **opt)
+    t = Tracker(d)
+    res["paper_electrodes"] = measure(t, d, n, losses=True)
+    base_surfs = list(d.surfaces)
+    d.surfaces = coated_table(base_surfs, ("gate",))
+    t.set_surfaces(d.surfaces)
+    res["paper_electrodes_gate_coated"] = measure(t, d, n)
+    t.close()
+    log(f"paper_electrodes: {res['paper_electrodes']}")
     return res
 
 
@@ -93,7 +110,7 @@ def main(argv=None):
     t0 = time.perf_counter()
     res = run(int(a.photons), log=lambda s: print(s, flush=True))
     print(json.dumps(dict(photons=int(a.photons), optics="paper best guess (Table 2)", ours=res, paper=PAPER,
-                          seconds=time.perf_counter() - t0)))
+                          paper_losses=PAPER_LOSSES, seconds=time.perf_counter() - t0)))
 
 
 if __name__ == "__main__":

@@ -79,3 +79,43 @@ def test_surfaces_have_no_open_edges(build):
     meets another surface; none is open, so no photon leaks through a gap."""
     uses = _edge_uses(build())
     assert uses.min() >= 2 and uses.max() <= 3
+
+
+@pytest.fixture(scope="module")
+def wires():
+    return g.darwin(electrode_kind="wires", **g.PAPER_OPTICS)
+
+
+def test_paper_wire_electrodes(wires):
+    """Five planes of parallel 200 um wires (Sec. 2.1, Table 1): 5 mm pitch
+    at z = 54, 12, 0 and 7.5 mm pitch at z = -2598, -2678, each prism 200 um
+    wide, each plane with its frame surface."""
+    d = wires
+    names = [s.name for s in d.surfaces]
+    for el in ("screen_top", "anode", "gate", "cathode", "screen_bottom"):
+        assert f"{el}_SS" in names and f"{el}_frame" in names
+    tv = d.verts[d.tris]
+    zc = tv.mean(1)[:, 2]
+    wire = d.mat_inner == g.OPAQUE
+    for zz, pitch in ((54, 5.0), (12, 5.0), (0, 5.0), (-2598, 7.5), (-2678, 7.5)):
+        m = wire & (np.abs(zc - zz) < 0.2)
+        n_wires = m.sum() // 8
+        assert abs(n_wires - 2 * (1290.0 * np.cos(np.pi / 24)) / pitch) < 4, (zz, n_wires)
+        # every wire triangle lies within 100 um of its plane
+        assert np.all(np.abs(tv[m][:, :, 2] - zz) <= 0.1 + 1e-4)
+    # top frames carry PTFE, bottom ones steel
+    assert d.surfaces[names.index("gate_frame")].reflectivity == d.surfaces[0].reflectivity
+    assert d.surfaces[names.index("cathode_frame")].reflectivity == 0.30
+
+
+def test_wire_layout_has_no_leaks_and_loss_table_closes(wires):
+    import oracle as O
+    from paper_2203_14354_gb300 import analysis
+    n = 20_000
+    r = O.Oracle(wires).propagate(n, seed=2)
+    assert r["fates"][4] == 0 and r["fates"][6] == 0
+    t = analysis.loss_table(wires, r["fates"], n)
+    parts = (sum(v for k, v in t.items() if k in ("LXe", "GXe", "quartz", "opaque")) + t["electrodes"] + t["pmt_caps"]
+             + t["ptfe"] + t["other_surfaces"] + t["escaped"] + t["truncated"])
+    assert parts == pytest.approx(t["not_detected"], abs=1e-9)
+    assert t["electrodes"] == pytest.approx(sum(t["electrode_parts"].values()))

@@ -1,5 +1,6 @@
 """Design variants (Sec. 5) on the GPU against the oracle, on the DARWIN-scale
-mesh without the wire meshes and with the paper's best-guess optics: per-array
+mesh without the wire meshes (and with the paper's five planes of parallel
+wires on frames) and with the paper's best-guess optics: per-array
 light collection agrees with the oracle, a single-phase detector collects
 more light and one without a bottom array far less (the paper's signs:
 +4.9 % abs. and 18 % against 43 %)."""
@@ -28,13 +29,14 @@ def run_both(det, seed=4):
 def results():
     res = {}
     for name, kw in (("baseline", {}), ("single_phase", dict(single_phase=True)),
-                     ("no_bottom_array", dict(bottom_array=False))):
+                     ("no_bottom_array", dict(bottom_array=False)),
+                     ("paper_electrodes", dict(electrode_kind="wires"))):
         det = g.darwin(electrodes=(), **g.PAPER_OPTICS, **kw)
         res[name] = (det, *run_both(det))
     return res
 
 
-@pytest.mark.parametrize("name", ["baseline", "single_phase", "no_bottom_array"])
+@pytest.mark.parametrize("name", ["baseline", "single_phase", "no_bottom_array", "paper_electrodes"])
 def test_variant_parity_with_oracle(results, name):
     det, a, b = results[name]
     top = det.pmt_array == 1
