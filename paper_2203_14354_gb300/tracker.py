@@ -16,7 +16,7 @@ import numpy as np
 import torch
 
 from . import _capi as A
-from .geometry import Detector, Source, SRC_EXPLICIT
+from .geometry import REFLECTOR, Detector, Source, SRC_EXPLICIT
 
 
 def _ptr(t):
@@ -145,7 +145,7 @@ class Tracker:
             v += [self.det.materials[m].abs_len_mm, self.det.materials[m].rayleigh_len_mm]
         for q in self.adj_surfs:
             sf = self.det.surfaces[q]
-            v.append(sf.reflectivity if sf.type == 1 else sf.transparency)
+            v.append(sf.reflectivity if sf.type == REFLECTOR else sf.transparency)
         return torch.tensor(v, dtype=torch.float64)
 
     def set_theta(self, theta):
@@ -157,7 +157,7 @@ class Tracker:
             k += 2
         for q in self.adj_surfs:
             sf = self.det.surfaces[q]
-            if sf.type == 1:
+            if sf.type == REFLECTOR:
                 sf.reflectivity = th[k]
             else:
                 sf.transparency = th[k]
