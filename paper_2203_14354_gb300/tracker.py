@@ -10,7 +10,6 @@ constructor raises if CUDA or the library is unavailable."""
 from __future__ import annotations
 
 import ctypes as C
-import math
 
 import numpy as np
 import torch
@@ -103,8 +102,9 @@ class Tracker:
         arr = (A.lxo_material * len(mats))()
         for i, m in enumerate(mats):
             arr[i].n = m.n
-            arr[i].abs_len_mm = m.abs_len_mm if math.isfinite(m.abs_len_mm) else float("inf")
-            arr[i].rayleigh_len_mm = m.rayleigh_len_mm if math.isfinite(m.rayleigh_len_mm) else float("inf")
+            # passed as given: inf means no process, NaN is rejected by the library
+            arr[i].abs_len_mm = m.abs_len_mm
+            arr[i].rayleigh_len_mm = m.rayleigh_len_mm
         self._check(self._L.lxo_set_materials(self._ctx, arr, len(mats)))
         self.n_materials = len(mats)
 

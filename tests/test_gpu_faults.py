@@ -49,6 +49,10 @@ def test_corrupt_mesh_and_bad_parameters_are_rejected(Tracker):
     mats[0].abs_len_mm = float("nan")
     with pytest.raises(LxoError, match="material"):
         trk.set_materials(mats)
+    surfs = [dataclasses.replace(sf) for sf in det.surfaces]
+    surfs[0].reflectivity = 1.2
+    with pytest.raises(LxoError, match="probability"):
+        trk.set_surfaces(surfs)
     ref = trk.propagate(2000, seed=1)
     again = trk.propagate(2000, seed=1)  # the rejected tables left the context as it was
     assert torch.equal(ref["fates"], again["fates"])
