@@ -255,3 +255,27 @@ def test_darwin_full_size_parity(darwin_pair):
         assert abs(pg - po) < 4 * sig2(po, n_gpu, n_o)
     # few leaks or geometry errors in a 1.8e7-triangle mesh
     assert gpu["fates"][4] + gpu["fates"][6] < 1e-4 * n_gpu
+
+
+def test_darwin_full_launch_sampled_ids(darwin_pair):
+    """The bench's full launch: 1e8 photons of the active-volume source in one
+    persistent launch, per-photon records kept; the oracle recomputes 100
+    blocks of 100 photon ids spread over the whole range, one by one, and
+    most end with the same fate and detail."""
+    det, trk, orc = darwin_pair
+    n = 100_000_000
+    base = 7 * n
+    gpu = trk.propagate(n, base=base, seed=1, per_photon=True, n_tbins=1)
+    assert int(gpu["fates"][:7].sum()) == n
+    fate = gpu["fate"].cpu().numpy()
+    detail = gpu["detail"].cpu().numpy()
+    del gpu
+    rng = np.random.default_rng(12)
+    starts = np.sort(rng.choice(n // 100, 100, replace=False)) * 100
+    agree = []
+    for s0 in starts:
+        ref = orc.propagate(100, base=base + int(s0), seed=1, per_photon=True, n_tbins=1)
+        agree.append((fate[s0:s0 + 100] == ref["fate"]) & (detail[s0:s0 + 100] == ref["detail"]))
+    agree = np.concatenate(agree)
+    assert agree.mean() > 0.9, agree.mean()
+    assert starts[-1] > 0.9 * n  # the sample reaches the end of the launch
