@@ -214,7 +214,7 @@ __device__ __forceinline__ void test_leaf(const Scene& sc, const WRay& wr, int r
 
 constexpr int kDone = INT32_MIN + 1;  // stack sentinel; never a valid leaf reference (< 2^28 records)
 
-// Resumable traversal state of one ray (its stack lives in a separate local
+// Traversal state of one ray (its stack lives in a separate local
 // array of kStackSize entries).
 struct TravState {
     WRay wr;
@@ -223,7 +223,6 @@ struct TravState {
     float bt;
     uint32_t best, best_rec;
     int node, leaf, sp;
-    uint32_t nodes0, leaves0;  // counters at the start (counting build only)
 };
 
 // Sets up the closest-hit query of ray (o, d) with t in (0, tmax], skipping
@@ -282,19 +281,14 @@ __device__ __forceinline__ void trav_begin(const Scene& sc, float3 o, float3 d, 
 // "While-while" traversal with postponed leaves (Aila & Laine, HPG 2009): a
 // lane that reaches a leaf parks it and keeps descending until every active
 // lane of the warp holds a leaf; then the warp tests leaves together.
-// Returns true when the query is complete.  With phys_min <= 32 it also
-// returns false (state saved, resumable) as soon as at least phys_min lanes
-// of the warp are no longer traversing, so that their photons can be
-// advanced together.
+// Runs the query to completion.
 template <bool kStats>
-__device__ bool trav_run(const Scene& sc, TravState& ts, int* stack, int* err, Counters& cnt, int phys_min)
+__device__ void trav_run(const Scene& sc, TravState& ts, int* stack, int* err, Counters& cnt)
 {
     int node = ts.node, leaf = ts.leaf, sp = ts.sp;
     float bt = ts.bt;
     uint32_t best = ts.best, best_rec = ts.best_rec;
-    bool done = false;
     while (true) {
-        bool yield = false;
         while (node >= 0) {
             if (kStats) {
                 cnt.nodes++;
@@ -335,14 +329,8 @@ __device__ bool trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
                 leaf = node;
                 node = stack[--sp];
             }
-            const uint32_t am = __activemask();
-            if (!__any_sync(am, leaf == 0)) break;
-            if (32 - __popc(am) >= phys_min) {
-                yield = true;
-                break;
-            }
+            if (!__any_sync(__activemask(), leaf == 0)) break;
         }
-        if (yield) break;
         if (node < 0 && node != kDone && leaf == 0) {  // a leaf reference taken from the stack
             leaf = node;
             node = stack[--sp];
@@ -356,11 +344,7 @@ __device__ bool trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
                 node = stack[--sp];
             }
         }
-        if (node == kDone) {
-            done = true;
-            break;
-        }
-        if (32 - __popc(__activemask()) >= phys_min) break;
+        if (node == kDone) break;
     }
     ts.node = node;
     ts.leaf = leaf;
@@ -368,7 +352,6 @@ __device__ bool trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
     ts.bt = bt;
     ts.best = best;
     ts.best_rec = best_rec;
-    return done;
 }
 
 __device__ __forceinline__ Hit trav_result(const TravState& ts)
@@ -382,7 +365,7 @@ __device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, f
     TravState ts;
     int stack[kStackSize];
     trav_begin(sc, o, d, skip, tmax, ts, stack);
-    trav_run<kStats>(sc, ts, stack, err, cnt, 33);
+    trav_run<kStats>(sc, ts, stack, err, cnt);
     return trav_result(ts);
 }
 
