@@ -37,13 +37,13 @@ OPS_PER_NODE, OPS_PER_TRI, OPS_PHYSICS = 40, 50, 250
 N_SM, LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) per photon of the propagation kernel: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of one timed launch on 2e6
-# photons of this workload (4.622 GB + 0.163 GB), divided by 2e6; scales with
+# photons of this workload (4.622 GB + 0.162 GB), divided by 2e6; scales with
 # the photon count.  None while the kernel differs from the one captured.
-DRAM_BYTES_PER_PHOTON = 2393
+DRAM_BYTES_PER_PHOTON = 2392
 # warp instructions issued per photon step by the same capture
-# (smsp__inst_executed.sum 1.266e10 over 5.15e7 steps); the issue-slot peak is
-# 152 SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
-WARP_INST_PER_STEP = 245.0
+# (smsp__inst_executed.sum 1.2662e10 over 5.152e7 steps); the issue-slot peak
+# is 152 SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
+WARP_INST_PER_STEP = 246.0
 SCHEDULERS_PER_SM = 4
 
 
