@@ -101,13 +101,74 @@ def run(n=10_000_000, electrodes=("gate", "anode", "cathode"), log=print):
     return res
 
 
+def lce_map(trk, det, n_z=50, n_r2=50, photons=1_000_000, r_max=1280.0, z_range=(-2597.0, -1.0), seed=0,
+            n_tbins=600, profile=g.NR_PROFILE):
+    """LCE and t90 on a Z x R^2 grid of isotropic point sources at x = 0
+    (Sec. 4.1: close to 2500 positions, 1e6 photons each), all of them in one
+    batched launch.  Returns LCE [n_z, n_r2] in %, top and bottom parts, t90
+    [n_z, n_r2] in ns, and the grid."""
+    import torch
+
+    zs = np.linspace(z_range[0], z_range[1], n_z)
+    r2 = (np.arange(n_r2) + 0.5) / n_r2 * r_max ** 2
+    ev = [(g.Source(g.SRC_POINT, g.LXE, center=(0.0, float(np.sqrt(q)), float(z))).with_profile(profile), photons)
+          for z in zs for q in r2]
+    trk.upload_events(ev)
+    out = trk.propagate_events(seed=seed, n_tbins=n_tbins, tbin_ns=1.0)
+    lce = out["lce"].to(torch.float64)
+    top = torch.from_numpy(det.pmt_array == 1).to(lce.device)
+    shape = (n_z, n_r2)
+    hist = out["hist"].sum(1).cpu().numpy()  # [E, B+1] summed over channels
+    del out
+    t90 = np.array([analysis.t90(h, 1.0) for h in hist]).reshape(shape)
+    return dict(z=zs, r2=r2, lce=(100.0 * lce.sum(1) / photons).cpu().numpy().reshape(shape),
+                top=(100.0 * lce[:, top].sum(1) / photons).cpu().numpy().reshape(shape),
+                bottom=(100.0 * lce[:, ~top].sum(1) / photons).cpu().numpy().reshape(shape), t90=t90)
+
+
+def map_summary(m):
+    """The features the paper reads off its maps (Sec. 4.1)."""
+    lce, top, bot, t90, z, r2 = m["lce"], m["top"], m["bottom"], m["t90"], m["z"], m["r2"]
+    prof_top, prof_bot = top.mean(1), bot.mean(1)
+    cross = np.nonzero(np.diff(np.sign(prof_top - prof_bot)))[0]
+    z_equal = float(np.interp(0.0, (prof_top - prof_bot)[cross[0]:cross[0] + 2], z[cross[0]:cross[0] + 2])) \
+        if cross.size else None
+    mid = slice(len(z) // 4, 3 * len(z) // 4)
+    inner = np.sqrt(m["r2"]) < np.sqrt(r2[-1]) - 20.0
+    radial = lce[mid][:, inner]
+    return dict(mean_lce=float(lce.mean()), mean_top=float(top.mean()), mean_bottom=float(bot.mean()),
+                z_equal_split=z_equal, z_top=float(z[-1]), z_bottom=float(z[0]),
+                radial_spread_mid_z=float((radial.max(1) - radial.min(1)).mean()),
+                bottom_edge_minus_bottom_centre=float(lce[0, -1] - lce[0, 0]),
+                top_edge_minus_top_centre=float(lce[-1, -1] - lce[-1, 0]),
+                mean_t90=float(np.mean(t90[np.isfinite(t90)])),
+                t90_near_bottom=float(np.mean(t90[0])), t90_middle=float(np.mean(t90[len(z) // 2])),
+                t90_near_top=float(np.mean(t90[-1])))
+
+
 def main(argv=None):
     import argparse
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--photons", type=float, default=1e7)
+    ap.add_argument("--map", action="store_true",
+                    help="LCE and t90 maps on a Z x R^2 grid (paper's electrode layout), not the variants")
+    ap.add_argument("--map-photons", type=float, default=1e6)
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
+    if a.map:
+        from .tracker import Tracker
+        det = g.darwin(electrode_kind="wires", **g.PAPER_OPTICS)
+        trk = Tracker(det)
+        t1 = time.perf_counter()
+        m = lce_map(trk, det, photons=int(a.map_photons))
+        trk.sync()
+        t_map = time.perf_counter() - t1
+        print(json.dumps(dict(sources=int(m["lce"].size), photons_per_source=int(a.map_photons),
+                              seconds_map=t_map, summary=map_summary(m),
+                              lce_on_axis=[round(float(x), 3) for x in m["lce"][:, 0]],
+                              t90_on_axis=[round(float(x), 1) for x in m["t90"][:, 0]])))
+        return
     res = run(int(a.photons), log=lambda s: print(s, flush=True))
     print(json.dumps(dict(photons=int(a.photons), optics="paper best guess (Table 2)", ours=res, paper=PAPER,
                           paper_losses=PAPER_LOSSES, seconds=time.perf_counter() - t0)))

@@ -119,3 +119,22 @@ def test_wire_layout_has_no_leaks_and_loss_table_closes(wires):
              + t["ptfe"] + t["other_surfaces"] + t["escaped"] + t["truncated"])
     assert parts == pytest.approx(t["not_detected"], abs=1e-9)
     assert t["electrodes"] == pytest.approx(sum(t["electrode_parts"].values()))
+
+
+def test_map_summary_reads_the_features():
+    """The map summary finds the height where top and bottom arrays collect
+    equally, the radial spread, the edge dips and the t90 profile, on
+    synthetic maps with known values."""
+    z = np.linspace(-2597.0, -1.0, 50)
+    r2 = (np.arange(50) + 0.5) / 50 * 1280.0 ** 2
+    top = np.tile(np.linspace(5.0, 40.0, 50)[:, None], (1, 50))
+    bot = np.tile(np.linspace(35.0, 10.0, 50)[:, None], (1, 50))
+    lce = top + bot
+    lce[0, -1] -= 7.0  # a dip at the bottom edge
+    t90 = np.tile(np.linspace(90.0, 150.0, 50)[:, None], (1, 50))
+    s = variants.map_summary(dict(z=z, r2=r2, lce=lce, top=top, bottom=bot, t90=t90))
+    # top = bottom where 5 + 35 f = 35 - 25 f, f = 0.5: mid-height
+    assert s["z_equal_split"] == pytest.approx(-1299.0, abs=1e-6)
+    assert s["radial_spread_mid_z"] == pytest.approx(0.0)
+    assert s["bottom_edge_minus_bottom_centre"] == pytest.approx(-7.0)
+    assert s["t90_near_bottom"] == pytest.approx(90.0) and s["t90_near_top"] == pytest.approx(150.0)
