@@ -101,6 +101,72 @@ def run(n=10_000_000, electrodes=("gate", "anode", "cathode"), log=print):
     return res
 
 
+# Sec. 4.1, LCE systematics: one parameter at a time over its spread (LCE %)
+PAPER_SYSTEMATICS = dict(L_abs_m=((20.0, 100.0), (32.0, 49.0)), L_ray_cm=((20.0, 50.0), (40.0, 45.0)),
+                         R_PTFE_LXe=((0.93, 1.00), (34.0, 45.0)))
+
+
+def systematics(trk, det, n=10_000_000, seed=0):
+    """The paper's one-at-a-time scans (Sec. 4.1) on the uploaded detector:
+    average LCE at each end of the spread of L_abs, L_Ray and the PTFE
+    reflectivity in LXe, the LCE against L_abs up to 1000 m, and the
+    first-order prediction of each end from the adjoint gradient at the
+    best-guess values (dLCE/dtheta = dE[detected]/dtheta / (QE n))."""
+    import torch
+
+    mats0 = [dataclasses_replace(m) for m in det.materials]
+    surfs0 = [dataclasses_replace(sf) for sf in det.surfaces]
+    qe = next(sf.qe for sf in det.surfaces if sf.type == g.PHOTOCATHODE)
+
+    def run(mats, surfs):
+        trk.set_materials(mats)
+        trk.set_surfaces(surfs)
+        out = trk.propagate(n, seed=seed, n_tbins=1)
+        return 100.0 * float(out["lce"].sum().item()) / n
+
+    def with_lxe(**kw):
+        mats = [dataclasses_replace(m) for m in mats0]
+        for k, v in kw.items():
+            setattr(mats[g.LXE], k, v)
+        return mats
+
+    def with_ptfe(r):
+        surfs = [dataclasses_replace(sf) for sf in surfs0]
+        surfs[0].reflectivity = r
+        return surfs
+
+    base = run(mats0, surfs0)
+    # gradient at the best-guess point: L_abs, L_ray of LXe and R of PTFE in LXe
+    trk.set_materials(mats0)
+    trk.set_surfaces(surfs0)
+    trk.set_adjoint([g.LXE], [0])
+    out = trk.propagate(n, seed=seed, n_tbins=1, adjoint=True)
+    grad = (trk.jacobian(out["adjoint"]).sum(0) / (qe * n) * 100.0).cpu().numpy()  # LCE % per unit
+    res = {"best_guess_lce": base, "gradient_lce_per_unit": {"L_abs_mm": float(grad[0]),
+                                                             "L_ray_mm": float(grad[1]),
+                                                             "R_PTFE_LXe": float(grad[2])}}
+    th0 = (mats0[g.LXE].abs_len_mm, mats0[g.LXE].rayleigh_len_mm, surfs0[0].reflectivity)
+    scans = {}
+    for name, (lo, hi), mk, q, scale in (("L_abs_m", (20.0, 100.0), lambda v: (with_lxe(abs_len_mm=v), surfs0), 0, 1e3),
+                                         ("L_ray_cm", (20.0, 50.0), lambda v: (with_lxe(rayleigh_len_mm=v), surfs0), 1, 10.0),
+                                         ("R_PTFE_LXe", (0.93, 1.00), lambda v: (mats0, with_ptfe(v)), 2, 1.0)):
+        ends = []
+        for v in (lo, hi):
+            ends.append(dict(value=v, lce=run(*mk(v * scale)),
+                             first_order=base + float(grad[q]) * (v * scale - th0[q])))
+        scans[name] = ends
+    res["scans"] = scans
+    res["lce_vs_L_abs_m"] = [(L, run(with_lxe(abs_len_mm=L * 1e3), surfs0)) for L in (20, 50, 100, 200, 300, 500, 1000)]
+    trk.set_materials(mats0)
+    trk.set_surfaces(surfs0)
+    return res
+
+
+def dataclasses_replace(x):
+    import dataclasses
+    return dataclasses.replace(x)
+
+
 def lce_map(trk, det, n_z=50, n_r2=50, photons=1_000_000, r_max=1280.0, z_range=(-2597.0, -1.0), seed=0,
             n_tbins=600, profile=g.NR_PROFILE):
     """LCE and t90 on a Z x R^2 grid of isotropic point sources at x = 0
@@ -154,8 +220,18 @@ def main(argv=None):
     ap.add_argument("--map", action="store_true",
                     help="LCE and t90 maps on a Z x R^2 grid (paper's electrode layout), not the variants")
     ap.add_argument("--map-photons", type=float, default=1e6)
+    ap.add_argument("--systematics", action="store_true",
+                    help="the paper's one-at-a-time LCE scans (paper's electrode layout), not the variants")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
+    if a.systematics:
+        from .tracker import Tracker
+        det = g.darwin(electrode_kind="wires", **g.PAPER_OPTICS)
+        trk = Tracker(det)
+        res = systematics(trk, det, n=int(a.photons))
+        print(json.dumps(dict(photons=int(a.photons), ours=res, paper=PAPER_SYSTEMATICS,
+                              seconds=time.perf_counter() - t0)))
+        return
     if a.map:
         from .tracker import Tracker
         det = g.darwin(electrode_kind="wires", **g.PAPER_OPTICS)
