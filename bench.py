@@ -63,11 +63,11 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(n, world):
+def workload_config(n, world, n_tris):
     return {"workload": "DARWIN-scale dual-phase TPC forward: 24-gon PTFE wall r=1300 mm, 889+889 3-inch PMTs, "
-                        "gate/anode/cathode hex wire meshes 216 um @ 5 mm, 1.78e7 triangles; photons uniform in the "
-                        "active LXe, isotropic, random linear polarisation, t=0, 175 nm",
-            "photons_per_step": int(n) * world, "photons_per_rank": int(n), "triangles": 17813848,
+                        f"gate/anode/cathode hex wire meshes 216 um @ 5 mm, {n_tris / 1e7:.2f}e7 triangles; photons "
+                        "uniform in the active LXe, isotropic, random linear polarisation, t=0, 175 nm",
+            "photons_per_step": int(n) * world, "photons_per_rank": int(n), "triangles": int(n_tris),
             "lxe_abs_m": 50, "lxe_rayleigh_cm": 40, "ptfe_R": [0.95, 0.70], "qe": 0.3,
             "time_bins_ns": "1000 x 1 ns + overflow", "l2": "inputs larger than L2 (BVH 1.3 GB), no flush",
             "parallelism": f"photon-id ranges per rank x{world}" if world > 1 else "single GPU"}
@@ -359,7 +359,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 physics / f32 intersection", "data": "synthetic",
             "impl": "reference",
-            "config": dict(workload_config(per_step, 1), sample=f"{per_step} photons per step on the CPU"),
+            "config": dict(workload_config(per_step, 1, det.n_tris), sample=f"{per_step} photons per step on the CPU"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} photons per step x {args.steps} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -493,7 +493,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(n, world),
+            "config": workload_config(n, world, det.n_tris),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "G lane-ops/s (FP32/INT32)", "frac": achieved / alu_peak,
                          "traffic": DRAM_BYTES_PER_PHOTON * n if DRAM_BYTES_PER_PHOTON else None,

@@ -1,0 +1,61 @@
+"""Host logic of bench.py without a GPU: the default launch (one GPU, K and W
+that finish within minutes, W >= 3), the clock summary of nvidia-smi samples
+(median under load, throttle reasons), the measured peaks, the workload
+description, and the reference arm's JSON line (the oracle timed on the
+host cores) on a small detector."""
+import io
+import json
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+
+import bench
+from paper_2203_14354_gb300 import geometry as g
+
+
+def test_default_launch(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.impl == "ours" and a.warmup >= 3 and 1 <= a.steps <= 10
+    assert a.photons == 1e8
+
+
+def test_clock_summary():
+    c = bench.ClockSampler(0)
+    c.rows = [["0", "2070", "2070", "500.1", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["0", "1980", "2070", "900.0", "Not Active", "Not Active", "Not Active", "Active"],
+              ["0", "2070", "2070", "[N/A]", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert bench.ClockSampler(0).summary()["reasons"] == ["unavailable"]
+
+
+def test_measured_peaks_and_workload():
+    peaks, kind = bench.measured_peaks()
+    assert kind in ("measured", "fallback") and peaks["hbm_gbs"] > 1000
+    cfg = bench.workload_config(100_000_000, 2, 17_927_640)
+    assert cfg["photons_per_step"] == 200_000_000 and cfg["photons_per_rank"] == 100_000_000
+    assert cfg["triangles"] == 17_927_640 and "1.79e7" in cfg["workload"]
+
+
+def test_reference_arm_line(monkeypatch):
+    monkeypatch.setattr(g, "darwin", lambda **kw: g.small_tpc())
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                                      "--cpu-seconds", "0.2"])
+    a = bench.parse()
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(a, 0, 1)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["metric"] == bench.METRIC and line["unit"] == "photons/s" and line["higher_is_better"]
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "photons/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    # other ranks print nothing
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(a, 1, 2)
+    assert buf.getvalue() == ""
