@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-adjoint-fd", action="store_true",
                     help="skip the 1e9-photon finite-difference check of the adjoint")
     ap.add_argument("--no-events", action="store_true", help="skip the batched-events measurement")
+    ap.add_argument("--no-calibration", action="store_true", help="skip the reduced calibration fit")
     return ap.parse_args()
 
 
@@ -281,6 +282,32 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
     return out
 
 
+def calibration_check():
+    """The gradient calibration on the 50 cm TPC (64 point sources x 2e5
+    photons, hidden L_abs 30 m, L_Ray 35 cm, R_PTFE 0.97 / 0.80, start at the
+    defaults): recovered values, their standard deviations from the Fisher
+    information, pulls, and the time per model launch."""
+    import torch
+    from paper_2203_14354_gb300 import calibrate, geometry, Tracker
+    det = geometry.scaled_tpc()
+    trk = Tracker(det)
+    trk.set_adjoint([geometry.LXE], [0, 1])
+    theta0 = trk.theta().tolist()
+    truth = [30_000.0, 350.0, 0.97, 0.80]
+    ev = geometry.calibration_sources(200_000, n_x=8, n_z=8, spacing=50.0, z_center=-250.0)
+    trk.upload_events(ev)
+    target = calibrate.hit_maps(trk, truth, seed=7)
+    cal = calibrate.Calibration(trk, ev, target, model_scale=2)
+    res = cal.fit(theta0)
+    rec = torch.tensor(res["theta"], dtype=torch.float64)
+    sigma = cal.covariance(rec, seed=98).diagonal().sqrt()
+    pull = (rec - torch.tensor(truth, dtype=torch.float64)) / sigma
+    return {"workload": "50 cm TPC, 64 point sources x 2e5 photons (model 2x), 4 parameters",
+            "params": ["L_abs_LXe_mm", "L_ray_LXe_mm", "R_PTFE_LXe", "R_PTFE_GXe"], "truth": truth,
+            "start": theta0, "recovered": res["theta"], "sigma": sigma.tolist(), "pull": pull.tolist(),
+            "launches": res["launches"], "scoring_steps": res["scoring_steps"], "seconds": res["seconds"]}
+
+
 def torch_bool(mask, device):
     import torch
     return torch.from_numpy(np.asarray(mask, bool)).to(device)
@@ -483,6 +510,7 @@ def main():
 
     adjoint = adjoint_cost(args) if (rank == 0 and not args.no_adjoint) else None
     events = events_throughput(det) if (rank == 0 and not args.no_events) else None
+    calibration = calibration_check() if (rank == 0 and not args.no_calibration) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -525,6 +553,8 @@ def main():
             line["adjoint"] = adjoint
         if events is not None:
             line["events"] = events
+        if calibration is not None:
+            line["calibration"] = calibration
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
