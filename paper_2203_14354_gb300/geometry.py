@@ -410,15 +410,43 @@ def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_p
 
 
 def _pmt_windows(b, centres, z_front, thickness, facing, r_window, r_pc, k_seg, mat_xe,
-                 surf_cap, surf_pc, chan0, rings=2):
+                 surf_cap, surf_pc, chan0, rings=2, cone_h=0.0, surf_cone=SURF_NONE):
     """Quartz windows: front face in the xenon (bare dielectric boundary), side
     wall and back-face annulus covered by the absorbing cap, photocathode disk
-    of radius ``r_pc`` on the back face (Sec. 2.1, Fig. 1)."""
+    of radius ``r_pc`` on the back face (Sec. 2.1, Fig. 1).  With cone_h > 0
+    a PTFE reflector of conical cross section sits on each window (Sec. 2.1):
+    a cone from the photocathode radius on the front face to the window
+    radius cone_h into the xenon, closed by a cylindrical collar at the
+    window radius; the front face is then bare only inside r_pc, the annulus
+    beyond it touches the PTFE (surface ``surf_cone``)."""
     z_back = z_front - facing * thickness
     for p, c in enumerate(centres):
         rim = _circle(c, r_window, k_seg)
         # front face, normal out of the quartz into the xenon
-        b.add(_disk(c, r_window, k_seg, z_front, rings), (0, 0, facing), QUARTZ, mat_xe)
+        if cone_h > 0.0:
+            inner = _circle(c, r_pc, k_seg)
+            b.add(_disk(c, r_pc, k_seg, z_front, rings), (0, 0, facing), QUARTZ, mat_xe)
+            b.add(_ring(rim, inner, z_front, c), (0, 0, facing), QUARTZ, OPAQUE, surf_cone)
+            z_top = z_front + facing * cone_h
+            phi = np.arctan2(inner[:, 1] - c[1], inner[:, 0] - c[0]) + math.pi / k_seg
+            phi = np.concatenate([phi, phi])
+            # cone: from (r_pc, z_front) to (r_window, z_top); normal from the
+            # xenon inside the opening into the PTFE
+            a0 = np.concatenate([inner, np.full((k_seg, 1), z_front)], 1)
+            a1 = np.concatenate([rim, np.full((k_seg, 1), z_top)], 1)
+            a0n, a1n = np.roll(a0, -1, 0), np.roll(a1, -1, 0)
+            cone = np.concatenate([np.stack([a0, a0n, a1n], 1), np.stack([a0, a1n, a1], 1)])
+            nrm = np.stack([cone_h * np.cos(phi), cone_h * np.sin(phi),
+                            np.full(phi.shape, -facing * (r_window - r_pc))], 1)
+            b.add(cone, nrm, mat_xe, OPAQUE, surf_cone)
+            # collar: cylinder at the window radius, xenon outside, PTFE inside
+            r0 = np.concatenate([rim, np.full((k_seg, 1), z_front)], 1)
+            r0n = np.roll(r0, -1, 0)
+            collar = np.concatenate([np.stack([r0, r0n, a1n], 1), np.stack([r0, a1n, a1], 1)])
+            b.add(collar, -np.stack([np.cos(phi), np.sin(phi), np.zeros_like(phi)], 1), mat_xe, OPAQUE,
+                  surf_cone)
+        else:
+            b.add(_disk(c, r_window, k_seg, z_front, rings), (0, 0, facing), QUARTZ, mat_xe)
         # side wall
         r0 = np.concatenate([rim, np.full((k_seg, 1), z_front)], 1)
         r1 = np.concatenate([rim, np.full((k_seg, 1), z_back)], 1)
@@ -689,7 +717,8 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
            r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lxe_ray_mm=400.0,
            r_ss=0.30, ss_spec_frac=2.0 / 3.0, k_seg=32, active_only=True, window_rings=2, plate_subdivide=False,
            ptfe_spec_frac=0.0, coated=(), r_coat=0.90, coat_spec_frac=0.85 / 0.90, single_phase=False,
-           bottom_array=True, r_ptfe_bottom=0.99, gxe_abs_mm=1e9, gxe_ray_mm=INF, electrode_kind="mesh"):
+           bottom_array=True, r_ptfe_bottom=0.99, gxe_abs_mm=1e9, gxe_ray_mm=INF, electrode_kind="mesh",
+           pmt_cones=0.0):
     """DARWIN-scale dual-phase TPC (Sec. 2.1, Table 1): 24-sided PTFE wall
     inscribed in r = 1300 mm; gate z = 0 (LXe), liquid surface z = +2, anode
     z = +8 (GXe), cathode z = -2598; hex-packed 3-inch windows (76.2 mm, 5 mm
@@ -716,7 +745,9 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
       z = 0 at 5 mm pitch, cathode z = -2598 and bottom screen z = -2678 at
       7.5 mm pitch, each fixed to a 24-gon frame 20 mm wide and 8 mm high
       (PTFE-covered on top, bare steel below; a surface entry of its own);
-      ``electrodes`` is ignored."""
+      ``electrodes`` is ignored;
+    * ``pmt_cones``: height (mm) of a conical PTFE reflector on each window
+      (Sec. 2.1; the paper gives no size: 0 = flat plates)."""
     R = 1300.0
     z_bot, z_cath, z_gate, z_liq, z_anode, z_top = -2688.0, -2598.0, 0.0, 2.0, 8.0, 64.0
     r_w, r_pc, thick = 38.1, 32.0, 5.0
@@ -742,8 +773,10 @@ def darwin(pitch_pmt=80.0, wire_um=216.0, mesh_pitch=5.0, electrodes=("gate", "a
     _wall(b, wall2, z_liq, z_top, gas, S_PTFE_G, top_pts=top_edge)
     if not single_phase:
         b.add(_fan(wall2, z_liq, (0, 0)), (0, 0, 1), LXE, GXE)
-    _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_pc, k_seg, LXE, S_CAP, S_PC, 0, rings=window_rings)
-    _pmt_windows(b, top, z_top, thick, -1, r_w, r_pc, k_seg, gas, S_CAP, S_PC, len(bot), rings=window_rings)
+    _pmt_windows(b, bot, z_bot, thick, +1, r_w, r_pc, k_seg, LXE, S_CAP, S_PC, 0, rings=window_rings,
+                 cone_h=pmt_cones, surf_cone=S_PTFE_L)
+    _pmt_windows(b, top, z_top, thick, -1, r_w, r_pc, k_seg, gas, S_CAP, S_PC, len(bot), rings=window_rings,
+                 cone_h=pmt_cones, surf_cone=S_PTFE_G)
     if electrode_kind == "wires":
         # (name, wire plane z, frame z range, xenon phase, pitch, frame surface)
         planes = (("screen_top", 54.0, (50.0, 58.0), gas, 5.0, S_PTFE_G),

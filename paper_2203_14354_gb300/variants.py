@@ -19,6 +19,11 @@ import numpy as np
 from . import analysis
 from . import geometry as g
 
+# The paper's own detector layout as far as it is described (Sec. 2.1): five
+# planes of parallel wires on frames, and a conical PTFE reflector on each
+# PMT window (6 mm high: the paper gives no size)
+PAPER_LAYOUT = dict(electrode_kind="wires", pmt_cones=6.0)
+
 # Sec. 5 results at L_abs = 50 m, best-guess optics (LCE %, top, bottom; t90 ns)
 PAPER = {
     "baseline": dict(lce=43.1, top=14.8, bottom=28.2, t90=200.0),
@@ -89,7 +94,7 @@ def run(n=10_000_000, electrodes=("gate", "anode", "cathode"), log=print):
         log(f"{name}: {res[name]}")
     res["single_phase"]["lce_change_abs"] = res["single_phase"]["lce"] - res["baseline"]["lce"]
     # the paper's own electrodes: five planes of parallel wires on frames
-    d = g.darwin(electrode_kind="wires", **opt)
+    d = g.darwin(**PAPER_LAYOUT, **opt)
     t = Tracker(d)
     res["paper_electrodes"] = measure(t, d, n, losses=True)
     base_surfs = list(d.surfaces)
@@ -226,7 +231,7 @@ def main(argv=None):
     t0 = time.perf_counter()
     if a.systematics:
         from .tracker import Tracker
-        det = g.darwin(electrode_kind="wires", **g.PAPER_OPTICS)
+        det = g.darwin(**PAPER_LAYOUT, **g.PAPER_OPTICS)
         trk = Tracker(det)
         res = systematics(trk, det, n=int(a.photons))
         print(json.dumps(dict(photons=int(a.photons), ours=res, paper=PAPER_SYSTEMATICS,
@@ -234,7 +239,7 @@ def main(argv=None):
         return
     if a.map:
         from .tracker import Tracker
-        det = g.darwin(electrode_kind="wires", **g.PAPER_OPTICS)
+        det = g.darwin(**PAPER_LAYOUT, **g.PAPER_OPTICS)
         trk = Tracker(det)
         t1 = time.perf_counter()
         m = lce_map(trk, det, photons=int(a.map_photons))

@@ -81,6 +81,20 @@ def test_surfaces_have_no_open_edges(build):
     assert uses.min() >= 2 and uses.max() <= 3
 
 
+def test_pmt_cones_close_the_windows():
+    """Conical PTFE reflectors on the windows: no open edge; the window rim
+    is shared by four surfaces (plate, window face, window side, collar)."""
+    d = g.darwin(electrodes=(), pmt_cones=6.0)
+    uses = _edge_uses(d)
+    assert uses.min() >= 2 and uses.max() <= 4
+    base = g.darwin(electrodes=())
+    # per window: an annulus of the front face turns into PTFE contact, plus cone and collar
+    assert d.n_tris > base.n_tris
+    z = d.verts[d.tris].mean(1)[:, 2]
+    cone = (d.mat_outer == g.OPAQUE) & (d.surface == 0) & (z > -2688.0) & (z < -2682.0)
+    assert cone.sum() == 889 * 4 * 32  # cone + collar, 2 x 32 triangles each, per bottom window
+
+
 @pytest.fixture(scope="module")
 def wires():
     return g.darwin(electrode_kind="wires", **g.PAPER_OPTICS)

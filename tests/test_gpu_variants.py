@@ -1,6 +1,7 @@
 """Design variants (Sec. 5) on the GPU against the oracle, on the DARWIN-scale
 mesh without the wire meshes (and with the paper's five planes of parallel
-wires on frames) and with the paper's best-guess optics: per-array
+wires on frames and PTFE cones on the windows) and with the paper's
+best-guess optics: per-array
 light collection agrees with the oracle, a single-phase detector collects
 more light and one without a bottom array far less (the paper's signs:
 +4.9 % abs. and 18 % against 43 %)."""
@@ -30,7 +31,7 @@ def results():
     res = {}
     for name, kw in (("baseline", {}), ("single_phase", dict(single_phase=True)),
                      ("no_bottom_array", dict(bottom_array=False)),
-                     ("paper_electrodes", dict(electrode_kind="wires"))):
+                     ("paper_electrodes", dict(electrode_kind="wires", pmt_cones=6.0))):
         det = g.darwin(electrodes=(), **g.PAPER_OPTICS, **kw)
         res[name] = (det, *run_both(det))
     return res
