@@ -112,3 +112,35 @@ def test_darwin_events_subset(tmp_path):
     s2 = out["lce"][48:][:, top].sum() / out["lce"][48:].sum()
     s1 = out["lce"][:48][:, top].sum() / out["lce"][:48].sum().clamp(min=1)
     assert float(s2) > float(s1)
+
+
+def test_darwin_events_full_size_sampled():
+    """The full batched-events workload: 4096 S1 + 512 S2 events, 2.6e8
+    photons, one launch. Sampled events (the largest among them) equal their
+    single-source runs bit for bit; the photons of one S1 and one S2 event
+    follow the oracle photon by photon."""
+    from paper_2203_14354_gb300 import Tracker
+    det = g.darwin()
+    ev = g.darwin_events(seed=0)
+    trk = Tracker(det)
+    trk.upload_events(ev)
+    out = trk.propagate_events(seed=4, n_tbins=64)
+    total = sum(n for _, n in ev)
+    assert int(out["fates"][:7].sum()) == total
+    rng = np.random.default_rng(2)
+    counts = np.array([n for _, n in ev])
+    pick = list(rng.choice(len(ev), 20, replace=False)) + [int(np.argmax(counts[:4096])),
+                                                         4096 + int(np.argmax(counts[4096:])),
+                                                         int(np.argmin(counts)), len(ev) - 1]
+    for e in pick:
+        src, n = ev[e]
+        one = trk.propagate(n, base=e << 32, seed=4, source=src, n_tbins=64)
+        assert torch.equal(one["det"], out["det"][e]) and torch.equal(one["hist"], out["hist"][e]), e
+    orc = O.Oracle(det)
+    for e in (int(np.argmin(np.where(counts[:4096] > 2000, counts[:4096], 1 << 40))), 4096):
+        src, n = ev[e]
+        m = min(n, 3000)
+        gp = trk.propagate(m, base=e << 32, seed=4, source=src, per_photon=True, n_tbins=1)
+        ref = orc.propagate(m, base=e << 32, seed=4, src=src, per_photon=True, n_tbins=1)
+        same = (gp["fate"].cpu().numpy() == ref["fate"]) & (gp["detail"].cpu().numpy() == ref["detail"])
+        assert same.mean() > 0.9, (e, same.mean())
