@@ -65,7 +65,8 @@ typedef struct lxo_ctx lxo_ctx;
 /* ---- tables (Table 2 of the paper; Sec. 2.2 surface models) ---------- */
 
 /* Bulk optical medium.  abs_len_mm / rayleigh_len_mm: mean free paths of
- * absorption and Rayleigh scattering (Table 2); +inf (or <= 0) = none. */
+ * absorption and Rayleigh scattering (Table 2); +inf (or <= 0) = none; NaN
+ * is rejected. */
 typedef struct {
     float n;
     float abs_len_mm;
@@ -206,7 +207,9 @@ typedef struct {
 
 /* ---- entry points ------------------------------------------------------ */
 
-/* Creates a context on CUDA device `cuda_device` (allocates its scratch). */
+/* Creates a context on CUDA device `cuda_device` (allocates its scratch).
+ * LXO_ERR_CUDA if the device cannot be used (no GPU: the library has no
+ * CPU fallback). */
 lxo_status lxo_create(lxo_ctx** out, int cuda_device);
 void lxo_destroy(lxo_ctx* ctx);
 const char* lxo_last_error(const lxo_ctx* ctx);
@@ -217,13 +220,20 @@ const char* lxo_last_error(const lxo_ctx* ctx);
  * mat_inner/mat_outer [nt] material on the side the geometric normal
  * (v1-v0)x(v2-v0) points away from / towards; surface [nt] surface index or
  * LXO_SURF_NONE; channel [nt] PMT channel of photocathode triangles, -1
- * elsewhere.  Copied; invalidates a previous BVH. */
+ * elsewhere.  Copied; invalidates a previous BVH.  LXO_ERR_ARG for
+ * 0 or >= 2^28 triangles, a vertex index >= nv or a non-finite vertex.
+ * Zero-area triangles are accepted and never hit. */
 lxo_status lxo_load_mesh(lxo_ctx* ctx, const float* verts, uint32_t nv, const uint32_t* tris, uint32_t nt,
                          const uint8_t* mat_inner, const uint8_t* mat_outer, const uint16_t* surface,
                          const int32_t* channel);
-/* Material table (Table 2).  Host array of n <= LXO_MAX_MATERIALS. */
+/* Material table (Table 2).  Host array of 1 <= n <= LXO_MAX_MATERIALS.
+ * LXO_ERR_ARG (table unchanged) if an index n is not > 0 or a length is NaN.
+ * A table change takes effect at the next propagation; it never rebuilds the
+ * BVH. */
 lxo_status lxo_set_materials(lxo_ctx* ctx, const lxo_material* m, uint32_t n);
-/* Surface table (Sec. 2.2).  Host array of n <= LXO_MAX_SURFACES. */
+/* Surface table (Sec. 2.2).  Host array of n <= LXO_MAX_SURFACES.
+ * LXO_ERR_ARG (table unchanged) for an unknown type or a probability
+ * (reflectivity, fractions, qe, transparency) outside [0, 1]. */
 lxo_status lxo_set_surfaces(lxo_ctx* ctx, const lxo_surface* s, uint32_t n);
 /* PMT table: n channels (the P of every per-channel tally). */
 lxo_status lxo_set_pmts(lxo_ctx* ctx, const lxo_pmt* p, uint32_t n);
