@@ -208,8 +208,8 @@ typedef struct {
 /* ---- entry points ------------------------------------------------------ */
 
 /* Creates a context on CUDA device `cuda_device` (allocates its scratch).
- * LXO_ERR_CUDA if the device cannot be used (no GPU: the library has no
- * CPU fallback). */
+ * LXO_ERR_CUDA if no CUDA device is usable (no GPU: the library has no CPU
+ * fallback), LXO_ERR_ARG for an index outside the devices. */
 lxo_status lxo_create(lxo_ctx** out, int cuda_device);
 void lxo_destroy(lxo_ctx* ctx);
 const char* lxo_last_error(const lxo_ctx* ctx);

@@ -37,5 +37,5 @@ def test_create_without_gpu_fails_cleanly():
         return
     L = _capi.lib()
     ctx = ctypes.c_void_p()
-    assert L.lxo_create(ctypes.byref(ctx), 0) != 0
+    assert L.lxo_create(ctypes.byref(ctx), 0) == _capi.LXO_ERR_CUDA  # no CPU fallback
     assert not ctx.value
