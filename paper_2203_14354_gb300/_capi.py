@@ -101,15 +101,21 @@ _SIGNATURES = {
 _lib = None
 
 
+def checked() -> bool:
+    """LXO_CHECKED=1 in the environment selects the checked build (every
+    kernel index compared with its array size; for debugging)."""
+    return os.environ.get("LXO_CHECKED", "0") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def lib():
     """The loaded library (built on first use)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build(checked=True) if checked() else _build.build()
         L = C.CDLL(path)
         for name, (res, args) in _SIGNATURES.items():
             f = getattr(L, name)

@@ -384,6 +384,8 @@ lxo_status lxo_build_bvh(lxo_ctx* c, const lxo_bvh_params* bp, lxo_bvh_info* inf
     sc.tris = c->d_tris;
     sc.n_tris = c->nt;
     sc.main_root = b.main_root;
+    sc.n_nodes = b.n_nodes;
+    sc.n_records = b.n_records;
     sc.n_clusters = b.n_clusters;
     for (int k = 0; k < b.n_clusters; ++k) {
         const lxo::ClusterHost& h = b.clusters[k];
@@ -670,7 +672,7 @@ lxo_status lxo_sync(lxo_ctx* c, void* stream)
     CK(cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "sync: read error word");
     if (h) {
         CK(cudaMemset(c->d_err, 0, sizeof(int)), "sync: clear error word");
-        return fail(c, LXO_ERR_DEVICE, "device fault flags 0x%x (1 = traversal stack, 2 = channel range)", h);
+        return fail(c, LXO_ERR_DEVICE, "device fault flags 0x%x (1 = traversal stack, 2 = channel range, 8 = index out of range)", h);
     }
     return LXO_OK;
 }

@@ -18,7 +18,9 @@ constexpr int kMaxTries = 64;
 constexpr int32_t kEmptyChild = INT32_MIN;  // child slot of a one-leaf root
 
 // device error word bits
-enum : int { kErrStack = 1, kErrChannel = 2, kErrTimeout = 4 };
+// device error bits: traversal stack overflow, PMT channel out of range,
+// an index out of its array (checked build only, LXO_CHECK_BOUNDS)
+enum : int { kErrStack = 1, kErrChannel = 2, kErrBounds = 8 };
 
 // Node: 64 bytes, boxes of both children (x, y, z slabs) + child references.
 //   f[0] = (c0.lo.x, c0.hi.x, c1.lo.x, c1.hi.x)
@@ -97,6 +99,7 @@ struct Scene {
     const float4* nodes;
     const float4* tris;    // records in leaf order
     uint32_t n_tris;
+    uint32_t n_nodes, n_records;  // array sizes (checked by the LXO_CHECK_BOUNDS build)
     int32_t main_root;     // kEmptyChild if every triangle is in a cluster
     int n_clusters;
     ClusterDev clusters[kMaxClusters];

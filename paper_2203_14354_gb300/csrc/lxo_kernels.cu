@@ -27,6 +27,13 @@
 namespace lxo {
 
 #define FULL_MASK 0xFFFFFFFFu
+// Checked build (a substitute for a memory checker): every BVH node,
+// triangle record, cell and tally row index is compared with its array size
+// before use; a bad one sets kErrBounds and ends the ray or skips the write,
+// never an out-of-range access.  Compiled out by default.
+#ifndef LXO_CHECK_BOUNDS
+#define LXO_CHECK_BOUNDS 0
+#endif
 constexpr int kPropThreadsK = 256;  // threads per CTA of the propagation kernel (stride of the adjoint tallies)
 
 // ---------------------------------------------------------------------------
@@ -188,10 +195,14 @@ __device__ __forceinline__ bool warp_leader()
 // exact watertight test, keeping (t, id) minimal in that order.
 template <bool kStats>
 __device__ __forceinline__ void test_leaf(const Scene& sc, const WRay& wr, int ref, uint32_t skip, float& bt,
-                                          uint32_t& best, uint32_t& best_rec, Counters& cnt)
+                                          uint32_t& best, uint32_t& best_rec, Counters& cnt, int* bounds_err)
 {
     const uint32_t enc = ~(uint32_t)ref;
     const uint32_t first = enc >> 3, count = (enc & 7u) + 1u;
+    if (LXO_CHECK_BOUNDS && (uint64_t)first + count > sc.n_records) {
+        atomicOr(bounds_err, kErrBounds);
+        return;
+    }
     if (kStats) {
         cnt.leaves++;
         cnt.tris += count;
@@ -265,6 +276,7 @@ __device__ __forceinline__ void trav_begin(const Scene& sc, float3 o, float3 d, 
             if ((fi1 - fi0 + 1.0f) * (fj1 - fj0 + 1.0f) <= (float)kMaxCellsPerRay) {
                 for (int j = (int)fj0; j <= (int)fj1; ++j)
                     for (int i = (int)fi0; i <= (int)fi1; ++i) {
+                        if (LXO_CHECK_BOUNDS && (i < 0 || j < 0 || i >= cl.nu || j >= cl.nv)) continue;
                         const int r = __ldg(&cl.cells[(size_t)j * cl.nu + i]);
                         if (r != kEmptyChild) stack[sp++] = r;
                     }
@@ -293,6 +305,12 @@ __device__ void trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
             if (kStats) {
                 cnt.nodes++;
                 if (warp_leader()) cnt.node_iters++;
+            }
+            if (LXO_CHECK_BOUNDS && (uint32_t)node >= sc.n_nodes) {
+                atomicOr(err, kErrBounds);
+                node = kDone;
+                sp = 1;
+                break;
             }
             const float4* nd = sc.nodes + 4 * (size_t)node;
             const float4 nx = __ldg(nd + 0), ny = __ldg(nd + 1), nz = __ldg(nd + 2);
@@ -337,7 +355,7 @@ __device__ void trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
         }
         while (leaf != 0) {
             if (kStats && warp_leader()) cnt.leaf_iters++;
-            test_leaf<kStats>(sc, ts.wr, leaf, ts.skip, bt, best, best_rec, cnt);
+            test_leaf<kStats>(sc, ts.wr, leaf, ts.skip, bt, best, best_rec, cnt, err);
             leaf = 0;
             if (node < 0 && node != kDone) {
                 leaf = node;
@@ -710,6 +728,11 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
     ph.time += h.t * mt.n_over_c;
     if (kAdjoint && ms >= 0) tl[(2 * ms) * kPropThreadsK] += h.t;
     // geometric normal and attributes of the triangle hit (record in leaf order)
+    if (LXO_CHECK_BOUNDS && h.rec >= p.sc.n_records) {
+        atomicOr(p.err, kErrBounds);
+        detail = (int)h.id;
+        return LXO_FATE_GEOM_ERR;
+    }
     const float4* tr = p.sc.tris + 3 * (size_t)h.rec;
     const float4 va = __ldg(tr + 0), vb = __ldg(tr + 1), vc = __ldg(tr + 2);
     const uint2 at = make_uint2(__float_as_uint(vc.z), __float_as_uint(vc.w));
@@ -828,6 +851,11 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
 {
     // row of the per-channel tallies: the channel, or event * P + channel for batched events
     const size_t row = p.n_events ? (size_t)(ph.pid >> 32) * p.n_chan + detail : (size_t)detail;
+    if (LXO_CHECK_BOUNDS && (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) &&
+        (detail < 0 || row >= (size_t)(p.n_events ? p.n_events : 1) * p.n_chan)) {
+        atomicOr(p.err, kErrBounds);
+        return;
+    }
     if (kAdjoint && fate == LXO_FATE_DETECTED)
         for (int k = 0; k < p.adj_k; ++k)
             atomicAdd(&p.out.adjoint[row * p.adj_k + k], (double)tl[k * kPropThreads]);
