@@ -39,3 +39,14 @@ def test_create_without_gpu_fails_cleanly():
     ctx = ctypes.c_void_p()
     assert L.lxo_create(ctypes.byref(ctx), 0) == _capi.LXO_ERR_CUDA  # no CPU fallback
     assert not ctx.value
+
+
+def test_checked_build_compiles_and_exports_every_symbol():
+    """The checked build (bounds compared inside the kernels) is a flag of the
+    same sources: it compiles for sm_103a and exports the same entry points."""
+    from paper_2203_14354_gb300 import build
+    path = build.build(checked=True)
+    assert path == build.LIB_CHECKED and path != build.LIB
+    lib = ctypes.CDLL(path)
+    for n in sorted(declared_symbols()):
+        assert hasattr(lib, n), n
