@@ -279,3 +279,21 @@ def test_darwin_full_launch_sampled_ids(darwin_pair):
     agree = np.concatenate(agree)
     assert agree.mean() > 0.9, agree.mean()
     assert starts[-1] > 0.9 * n  # the sample reaches the end of the launch
+
+
+def test_darwin_every_pmt_within_4_sigma(darwin_pair):
+    """The method's per-PMT criterion on the full DARWIN-scale mesh: the same
+    2e6 photon ids on both sides, every one of the 1778 PMTs' light
+    collection (and detected) fraction within 4 sigma binomial of the
+    oracle's, the total light collection within 2 %."""
+    det, trk, orc = darwin_pair
+    n = 2_000_000
+    gpu = np_out(trk.propagate(n, base=3 << 30, seed=5, n_tbins=1))
+    ref = orc.propagate(n, base=3 << 30, seed=5, n_tbins=1)
+    for key in ("lce", "det"):
+        g_, o_ = gpu[key].astype(np.float64), ref[key].astype(np.float64)
+        p = o_ / n
+        sig = np.sqrt(np.maximum(p * (1 - p), 1.0 / n) * 2.0 / n)
+        z = np.abs(g_ - o_) / n / sig
+        assert z.max() < 4.0, (key, int(z.argmax()), z.max())
+    assert abs(gpu["lce"].sum() - ref["lce"].sum()) < 0.02 * ref["lce"].sum()
