@@ -285,11 +285,12 @@ def test_darwin_every_pmt_within_4_sigma(darwin_pair):
     """The method's per-PMT criterion on the full DARWIN-scale mesh: the same
     2e6 photon ids on both sides, every one of the 1778 PMTs' light
     collection (and detected) fraction within 4 sigma binomial of the
-    oracle's, the total light collection within 2 %."""
+    oracle's, the total light collection within 2 %, the arrival-time
+    distributions within 0.01 in CDF."""
     det, trk, orc = darwin_pair
     n = 2_000_000
-    gpu = np_out(trk.propagate(n, base=3 << 30, seed=5, n_tbins=1))
-    ref = orc.propagate(n, base=3 << 30, seed=5, n_tbins=1)
+    gpu = np_out(trk.propagate(n, base=3 << 30, seed=5, n_tbins=500))
+    ref = orc.propagate(n, base=3 << 30, seed=5, n_tbins=500)
     for key in ("lce", "det"):
         g_, o_ = gpu[key].astype(np.float64), ref[key].astype(np.float64)
         p = o_ / n
@@ -297,3 +298,7 @@ def test_darwin_every_pmt_within_4_sigma(darwin_pair):
         z = np.abs(g_ - o_) / n / sig
         assert z.max() < 4.0, (key, int(z.argmax()), z.max())
     assert abs(gpu["lce"].sum() - ref["lce"].sum()) < 0.02 * ref["lce"].sum()
+    # arrival times of the detected photons, summed over PMTs (1 ns bins + overflow)
+    cg = np.cumsum(gpu["hist"].sum(0)) / gpu["hist"].sum()
+    co = np.cumsum(ref["hist"].sum(0)) / ref["hist"].sum()
+    assert np.abs(cg - co).max() < 0.01
