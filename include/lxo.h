@@ -25,8 +25,8 @@
  *    stream depends only on (seed, p), so splitting a run into several calls
  *    with disjoint photon_id_base ranges adds up to the same tallies.
  *
- * Units: mm, ns.  Speed of light 299.792458 mm/ns; a photon moves at c/n of
- * the medium it is in.
+ * Units: mm, ns, nm (wavelength).  Speed of light 299.792458 mm/ns; a photon
+ * moves at c/n of the medium it is in.
  *
  * Random numbers (identical in every implementation of this method): photon p
  * uses Philox4x32-10 (Salmon et al., SC'11) with key = (seed low 32 bits, seed
@@ -38,7 +38,9 @@
  * draw 1 (and 2, 3, ... for Rayleigh rejection tries) gives new directions.
  * The emission-time draw of a source with a scintillation time profile is
  * (step 0xFFFFFFFF, draw 0xFFFFFFFF): u0 < singlet_frac picks the singlet
- * component, and the delay is -tau ln u1 of the component picked.
+ * component, and the delay is -tau ln u1 of the component picked.  The same
+ * draw gives the wavelength of a source with a spectrum (Box-Muller):
+ * z = sqrt(-2 ln u2) cos(2 pi u3).
  */
 #ifndef LXO_H
 #define LXO_H
@@ -64,13 +66,28 @@ typedef struct lxo_ctx lxo_ctx;
 
 /* ---- tables (Table 2 of the paper; Sec. 2.2 surface models) ---------- */
 
+/* Wavelength at which every material constant is quoted (Table 2 gives the
+ * optical properties at 175 nm). */
+#define LXO_REF_WAVELENGTH_NM 175.0f
+
 /* Bulk optical medium.  abs_len_mm / rayleigh_len_mm: mean free paths of
  * absorption and Rayleigh scattering (Table 2); +inf (or <= 0) = none; NaN
- * is rejected. */
+ * is rejected.  n, abs_len_mm and rayleigh_len_mm hold at
+ * LXO_REF_WAVELENGTH_NM.  The paper uses these mean-wavelength values for
+ * every photon of its spectrum (Sec. 2.2), which is dn_dlambda_per_nm = 0 and
+ * rayleigh_exp = 0.  Otherwise, for a photon of wavelength lambda (nm):
+ *   n(lambda)            = n + dn_dlambda_per_nm * (lambda - LXO_REF_WAVELENGTH_NM)
+ *   rayleigh_len(lambda) = rayleigh_len_mm * (lambda / LXO_REF_WAVELENGTH_NM)^rayleigh_exp
+ * (rayleigh_exp = 4 is Rayleigh's lambda^-4 law); n(lambda) also sets the
+ * speed c / n(lambda).  Both must be finite (LXO_ERR_ARG); a propagation whose
+ * source spectrum reaches a wavelength with n(lambda) <= 0 fails with
+ * LXO_ERR_ARG. */
 typedef struct {
     float n;
     float abs_len_mm;
     float rayleigh_len_mm;
+    float dn_dlambda_per_nm;
+    float rayleigh_exp;
 } lxo_material;
 
 /* surface model types */
@@ -135,6 +152,15 @@ typedef struct {
     float singlet_frac;
     float tau_singlet_ns;
     float tau_triplet_ns;
+    /* emission spectrum (Sec. 2.2, Table 2: a Gaussian of mean 174.8 nm and
+     * FWHM 10.2 nm for LXe): photon wavelength wl_mean_nm + sigma * z with
+     * sigma = wl_fwhm_nm / (2 sqrt(2 ln 2)) and z a standard normal deviate
+     * (|z| <= 5.8).  wl_mean_nm = 0 means LXO_REF_WAVELENGTH_NM; wl_fwhm_nm = 0
+     * gives one wavelength.  Both must be finite and >= 0, and the spectrum
+     * must stay above 0 nm.  It changes the path of a photon only through the
+     * dispersion of lxo_material. */
+    float wl_mean_nm;
+    float wl_fwhm_nm;
     const float* pos;     /* EXPLICIT only, device [n*3] */
     const float* dir;     /* EXPLICIT only, device [n*3], unit */
     const float* pol;     /* EXPLICIT only, device [n*3], unit, made perpendicular to dir */
@@ -227,7 +253,8 @@ lxo_status lxo_load_mesh(lxo_ctx* ctx, const float* verts, uint32_t nv, const ui
                          const uint8_t* mat_inner, const uint8_t* mat_outer, const uint16_t* surface,
                          const int32_t* channel);
 /* Material table (Table 2).  Host array of 1 <= n <= LXO_MAX_MATERIALS.
- * LXO_ERR_ARG (table unchanged) if an index n is not > 0 or a length is NaN.
+ * LXO_ERR_ARG (table unchanged) if an index n is not > 0, a length is NaN or
+ * a dispersion field is not finite.
  * A table change takes effect at the next propagation; it never rebuilds the
  * BVH. */
 lxo_status lxo_set_materials(lxo_ctx* ctx, const lxo_material* m, uint32_t n);
@@ -253,9 +280,12 @@ lxo_status lxo_trace_rays(lxo_ctx* ctx, const float* org, const float* dir, cons
 
 /* The first state of photons base .. base+n-1 from a source: device arrays
  * pos, dir, pol [n*3] (float) and, if not NULL, the emission time [n] (ns;
- * t0 plus the delay of the source's scintillation time profile). */
+ * t0 plus the delay of the source's scintillation time profile) and the
+ * wavelength [n] (nm, drawn from the source's spectrum; a photon keeps it to
+ * its fate). */
 lxo_status lxo_sample_source(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
-                             uint64_t seed, float* pos, float* dir, float* pol, float* time, void* stream);
+                             uint64_t seed, float* pos, float* dir, float* pol, float* time, float* wavelength,
+                             void* stream);
 
 /* Propagates photons base .. base+n-1 to their fates and accumulates the
  * tallies into `out` (device buffers, caller-owned, zeroed by the caller).
@@ -286,6 +316,8 @@ typedef struct {
     float singlet_frac;   /* scintillation time profile, as in lxo_source */
     float tau_singlet_ns;
     float tau_triplet_ns;
+    float wl_mean_nm;     /* emission spectrum, as in lxo_source */
+    float wl_fwhm_nm;
     float reserved;
     uint64_t n_photons;   /* < 2^32 */
 } lxo_event;

@@ -53,7 +53,7 @@ def lib():
         L.orc_set_channels.argtypes = [C.c_void_p, C.c_int]
         L.orc_trace.argtypes = [C.c_void_p, C.c_uint64, f32p, f32p, C.c_void_p, C.c_void_p, u32p, f32p, C.c_int]
         L.orc_sample_source.argtypes = [C.c_void_p, C.POINTER(_Source), C.c_uint64, C.c_uint64, C.c_uint64,
-                                        f64p, f64p, f64p, i32p, f64p]
+                                        f64p, f64p, f64p, i32p, f64p, f64p]
         L.orc_propagate.restype = C.c_int
         L.orc_propagate.argtypes = [C.c_void_p, C.POINTER(_Source), C.c_uint64, C.c_uint64, C.c_uint64,
                                     C.c_uint32, C.c_double, C.c_uint32, C.POINTER(_Results), C.c_int]
@@ -79,7 +79,8 @@ def _ptr(a):
 
 def source_array(src) -> np.ndarray:
     return np.array([src.kind, src.medium, src.n_sides, src.radius, src.phase, src.z_min, src.z_max,
-                     *src.center, *src.p1, src.t0, src.singlet_frac, src.tau_singlet_ns, src.tau_triplet_ns],
+                     *src.center, *src.p1, src.t0, src.singlet_frac, src.tau_singlet_ns, src.tau_triplet_ns,
+                     src.wl_mean_nm, src.wl_fwhm_nm],
                     np.float64)
 
 
@@ -98,7 +99,8 @@ class Oracle:
                                   np.ascontiguousarray(det.surface), np.ascontiguousarray(det.channel))
         if not self._s:
             raise ValueError("oracle rejected the mesh")
-        m = np.array([[x.n, x.abs_len_mm, x.rayleigh_len_mm] for x in det.materials], np.float64).ravel()
+        m = np.array([[x.n, x.abs_len_mm, x.rayleigh_len_mm, x.dn_dlambda_per_nm, x.rayleigh_exp]
+                      for x in det.materials], np.float64).ravel()
         assert L.orc_set_materials(self._s, m, self.n_mat) == 0
         if self.n_surf:
             t = np.array([x.type for x in det.surfaces], np.int32)
@@ -157,14 +159,16 @@ class Oracle:
             s.explicit_pos, s.explicit_dir, s.explicit_pol = _ptr(pos), _ptr(dir), _ptr(pol)
         return s, keep
 
-    def sample_source(self, n, base=0, seed=0, src=None, explicit=None, time=False):
-        """First photon states (pos, dir, pol [n, 3], medium [n]; and emission times [n] if time)."""
+    def sample_source(self, n, base=0, seed=0, src=None, explicit=None, time=False, wavelength=False):
+        """First photon states: pos, dir, pol [n, 3], medium [n]; then the
+        emission times [n] if time, and the wavelengths [n] (nm) if wavelength."""
         s, keep = self._source(src or self.det.source, explicit)
         pos = np.empty((n, 3)); dir = np.empty((n, 3)); pol = np.empty((n, 3))
         med = np.empty(n, np.int32)
         t = np.empty(n)
-        lib().orc_sample_source(self._s, C.byref(s), n, base, seed, pos, dir, pol, med, t)
-        return (pos, dir, pol, med, t) if time else (pos, dir, pol, med)
+        wl = np.empty(n)
+        lib().orc_sample_source(self._s, C.byref(s), n, base, seed, pos, dir, pol, med, t, wl)
+        return (pos, dir, pol, med) + ((t,) if time else ()) + ((wl,) if wavelength else ())
 
     def propagate(self, n, base=0, seed=0, src=None, explicit=None, max_steps=10000, tbin_ns=1.0,
                   n_tbins=1000, per_photon=False, threads=None, adjoint=False):

@@ -23,6 +23,8 @@
 #define TWO_PI 6.283185307179586
 #define PI_D 3.141592653589793
 #define SOURCE_STEP 0xFFFFFFFFu
+/* Table 2 quotes every optical constant at 175 nm */
+#define REF_WAVELENGTH_NM 175.0
 #define MAX_TRIES 64
 #define N_FIXED 8 /* fate counters before the per-material block */
 
@@ -39,7 +41,7 @@ struct orc_scene {
     onode* nodes;
     uint32_t n_nodes;
     int n_mat;
-    double mat[64][3];
+    double mat[64][5];  /* n, L_abs, L_ray (at the reference wavelength), dn/dlambda per nm, Rayleigh exponent */
     int n_surf;
     int stype[256];
     double sp[256][6];
@@ -319,7 +321,7 @@ int orc_set_materials(orc_scene* s, const double* m, int n)
 {
     if (n < 1 || n > 64) return -1;
     for (int i = 0; i < n; ++i)
-        for (int j = 0; j < 3; ++j) s->mat[i][j] = m[3 * i + j];
+        for (int j = 0; j < 5; ++j) s->mat[i][j] = m[5 * i + j];
     s->n_mat = n;
     return 0;
 }
@@ -605,7 +607,7 @@ static int inside_polygon(double x, double y, int n, double R, double phase)
 }
 
 static void source_photon(const orc_source* src, uint64_t pid, uint64_t idx, uint64_t seed,
-                          double pos[3], double dir[3], double pol[3], int* medium, double* t0)
+                          double pos[3], double dir[3], double pol[3], int* medium, double* t0, double* wl)
 {
     const double* p = src->src;
     int kind = (int)p[0];
@@ -620,6 +622,17 @@ static void source_photon(const orc_source* src, uint64_t pid, uint64_t idx, uin
         draw4(seed, pid, SOURCE_STEP, 0xFFFFFFFFu, w);
         double tau = w[0] < p[14] ? p[15] : p[16];
         *t0 += -tau * log(w[1]);
+    }
+    /* emission spectrum (Sec. 2.2, Table 2): a Gaussian of mean p[17] (0 =
+     * the reference wavelength) and full width at half maximum p[18], so
+     * sigma = FWHM / (2 sqrt(2 ln 2)); the standard normal deviate is the
+     * Box-Muller transform of u2, u3 of the emission draw */
+    *wl = p[17] > 0.0 ? p[17] : REF_WAVELENGTH_NM;
+    if (p[18] > 0.0) {
+        double w[4];
+        draw4(seed, pid, SOURCE_STEP, 0xFFFFFFFFu, w);
+        double sigma = p[18] / (2.0 * sqrt(2.0 * log(2.0)));
+        *wl += sigma * sqrt(-2.0 * log(w[2])) * cos(TWO_PI * w[3]);
     }
     if (kind == ORC_SRC_EXPLICIT) {
         for (int a = 0; a < 3; ++a) {
@@ -673,15 +686,16 @@ static void source_photon(const orc_source* src, uint64_t pid, uint64_t idx, uin
 }
 
 void orc_sample_source(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
-                       double* pos, double* dir, double* pol, int* medium, double* time)
+                       double* pos, double* dir, double* pol, int* medium, double* time, double* wavelength)
 {
     (void)s;
     for (uint64_t i = 0; i < n; ++i) {
-        double t0;
+        double t0, wl;
         int m;
-        source_photon(src, base + i, i, seed, &pos[3 * i], &dir[3 * i], &pol[3 * i], &m, &t0);
+        source_photon(src, base + i, i, seed, &pos[3 * i], &dir[3 * i], &pol[3 * i], &m, &t0, &wl);
         if (medium) medium[i] = m;
         if (time) time[i] = t0;
+        if (wavelength) wavelength[i] = wl;
     }
 }
 
@@ -702,6 +716,19 @@ typedef struct {
     double* adj;
 } tally;
 
+/* Dispersion about the reference wavelength, for a photon of wavelength wl
+ * (nm): index n + dn/dlambda (wl - 175), Rayleigh length L_ray (wl/175)^p.
+ * With dn/dlambda = 0 and p = 0 every photon sees the Table 2 constants. */
+static double index_at(const double* mat, double wl)
+{
+    return mat[0] + mat[3] * (wl - REF_WAVELENGTH_NM);
+}
+
+static double rayleigh_len_at(const double* mat, double wl)
+{
+    return mat[4] == 0.0 ? mat[2] : mat[2] * pow(wl / REF_WAVELENGTH_NM, mat[4]);
+}
+
 static void spawn_offset(double pos[3], const double o_ray[3], double t_hit, const double N[3], double side)
 {
     double m = 1.0;
@@ -717,9 +744,9 @@ static void spawn_offset(double pos[3], const double o_ray[3], double t_hit, con
 static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, uint64_t idx, uint64_t seed,
                        uint32_t max_steps, double tbin, uint32_t n_tbins, tally* ty, orc_results* out)
 {
-    double pos[3], dir[3], pol[3], time;
+    double pos[3], dir[3], pol[3], time, wl;
     int medium;
-    source_photon(src, pid, idx, seed, pos, dir, pol, &medium, &time);
+    source_photon(src, pid, idx, seed, pos, dir, pol, &medium, &time, &wl);
     uint32_t last = NO_HIT;
     uint32_t fate = ORC_TRUNCATED;
     int32_t detail = -1;
@@ -732,14 +759,14 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
         draw4(seed, pid, step, 0, u);
         const double* mat = s->mat[medium];
         double d_abs = isinf(mat[1]) ? INFINITY : -mat[1] * log(u[0]);
-        double d_ray = isinf(mat[2]) ? INFINITY : -mat[2] * log(u[1]);
+        double d_ray = isinf(mat[2]) ? INFINITY : -rayleigh_len_at(mat, wl) * log(u[1]);
         double d_int = d_abs < d_ray ? d_abs : d_ray;
         float of[3] = {(float)pos[0], (float)pos[1], (float)pos[2]};
         float df[3] = {(float)dir[0], (float)dir[1], (float)dir[2]};
         float tmax = isinf(d_int) ? INFINITY : (float)d_int;
         float th;
         uint32_t tri = closest_hit(s, of, df, last, tmax, &th, 0);
-        double vel = C_MM_PER_NS / mat[0];
+        double vel = C_MM_PER_NS / index_at(mat, wl);
         const int ms = s->mat_slot[medium];
         if (tri == NO_HIT) {
             if (isinf(d_int)) { fate = ORC_ESCAPED; detail = -1; break; }
@@ -777,7 +804,8 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
         if (sid == SURF_NONE) {
             if (from != medium || to >= M) { fate = ORC_GEOM_ERR; detail = (int32_t)tri; break; }
             double k2[3], e2[3];
-            int refl = orc_dielectric(dir, pol, Nf, s->mat[from][0], s->mat[to][0], u[2], k2, e2, NULL);
+            int refl = orc_dielectric(dir, pol, Nf, index_at(s->mat[from], wl), index_at(s->mat[to], wl), u[2],
+                                      k2, e2, NULL);
             memcpy(dir, k2, sizeof k2);
             memcpy(pol, e2, sizeof e2);
             if (!refl) medium = to;

@@ -45,7 +45,9 @@ orc_scene* orc_scene_new(const float* verts, uint32_t nv, const uint32_t* tris, 
                          const uint8_t* mat_inner, const uint8_t* mat_outer,
                          const uint16_t* surface, const int32_t* channel);
 void orc_scene_free(orc_scene* s);
-/* materials: [n*3] = {refractive index, absorption length mm, Rayleigh length mm}; inf = none */
+/* materials: [n*5] = {refractive index, absorption length mm, Rayleigh length mm (inf = none), all at
+ * 175 nm; dn/dlambda per nm; Rayleigh-length exponent p}: a photon of wavelength wl sees the index
+ * n + dn/dlambda (wl - 175) and the Rayleigh length L (wl / 175)^p */
 int orc_set_materials(orc_scene* s, const double* m, int n);
 /* surfaces: types[n]; params [n*6] = {R, spec_frac, qe, T, R_wire, wire_spec_frac} */
 int orc_set_surfaces(orc_scene* s, const int* types, const double* p, int n);
@@ -59,7 +61,9 @@ void orc_trace(const orc_scene* s, uint64_t n, const float* org, const float* di
 /* source description packed as doubles:
  * [0] kind [1] medium [2] n_sides [3] radius [4] phase [5] z_min [6] z_max
  * [7..9] center [10..12] p1 [13] t0 [14] singlet fraction [15] singlet and
- * [16] triplet time constants (ns; both 0 = no emission delay).
+ * [16] triplet time constants (ns; both 0 = no emission delay) [17] mean
+ * wavelength (nm; 0 = 175) and [18] FWHM of the Gaussian emission spectrum
+ * (nm; 0 = one wavelength).
  * explicit_* used for ORC_SRC_EXPLICIT ([n*3] each). */
 typedef struct {
     const double* src;
@@ -69,9 +73,9 @@ typedef struct {
 } orc_source;
 
 /* source sampling only (first photon state), positions/dirs/pols [n*3];
- * medium [n] and emission time [n] (ns) may be NULL */
+ * medium [n], emission time [n] (ns) and wavelength [n] (nm) may be NULL */
 void orc_sample_source(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
-                       double* pos, double* dir, double* pol, int* medium, double* time);
+                       double* pos, double* dir, double* pol, int* medium, double* time, double* wavelength);
 
 typedef struct {
     uint64_t* lce;        /* [P] photocathode arrivals */

@@ -18,11 +18,13 @@ LXO_NO_HIT = 0xFFFFFFFF
 LXO_FLAG_STATS = 1
 LXO_FLAG_ADJOINT = 2
 LXO_STATIC_SCRATCH_BYTES = 8 << 20
+LXO_REF_WAVELENGTH_NM = 175.0
 FATE_NAMES = ["detected", "qe_fail", "bulk_abs", "surf_abs", "escaped", "truncated", "geom_err"]
 
 
 class lxo_material(C.Structure):
-    _fields_ = [("n", C.c_float), ("abs_len_mm", C.c_float), ("rayleigh_len_mm", C.c_float)]
+    _fields_ = [("n", C.c_float), ("abs_len_mm", C.c_float), ("rayleigh_len_mm", C.c_float),
+                ("dn_dlambda_per_nm", C.c_float), ("rayleigh_exp", C.c_float)]
 
 
 class lxo_surface(C.Structure):
@@ -39,14 +41,15 @@ class lxo_source(C.Structure):
                 ("radius", C.c_float), ("phase", C.c_float), ("z_min", C.c_float), ("z_max", C.c_float),
                 ("center", C.c_float * 3), ("p1", C.c_float * 3), ("t0", C.c_float),
                 ("singlet_frac", C.c_float), ("tau_singlet_ns", C.c_float), ("tau_triplet_ns", C.c_float),
+                ("wl_mean_nm", C.c_float), ("wl_fwhm_nm", C.c_float),
                 ("pos", C.c_void_p), ("dir", C.c_void_p), ("pol", C.c_void_p)]
 
 
 class lxo_event(C.Structure):
     _fields_ = [("kind", C.c_int32), ("medium", C.c_int32), ("center", C.c_float * 3), ("p1", C.c_float * 3),
                 ("radius", C.c_float), ("t0", C.c_float), ("singlet_frac", C.c_float),
-                ("tau_singlet_ns", C.c_float), ("tau_triplet_ns", C.c_float), ("reserved", C.c_float),
-                ("n_photons", C.c_uint64)]
+                ("tau_singlet_ns", C.c_float), ("tau_triplet_ns", C.c_float), ("wl_mean_nm", C.c_float),
+                ("wl_fwhm_nm", C.c_float), ("reserved", C.c_float), ("n_photons", C.c_uint64)]
 
 
 class lxo_run_params(C.Structure):
@@ -83,7 +86,7 @@ _SIGNATURES = {
     "lxo_build_bvh": (C.c_int, [vp, C.POINTER(lxo_bvh_params), C.POINTER(lxo_bvh_info)]),
     "lxo_trace_rays": (C.c_int, [vp, vp, vp, vp, vp, C.c_uint32, vp, vp, vp]),
     "lxo_sample_source": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, vp, vp,
-                                     vp]),
+                                     vp, vp]),
     "lxo_propagate": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64, C.POINTER(lxo_run_params),
                                 C.POINTER(lxo_results), vp]),
     "lxo_propagate_host": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,

@@ -117,6 +117,37 @@ lxo_status validate(lxo_ctx* c)
     return LXO_OK;
 }
 
+// Largest |z| of the Box-Muller deviate: sqrt(-2 ln u) with u >= 2^-24 (the
+// uniforms of the draw contract) is at most 5.77.
+constexpr double kMaxDeviate = 5.8;
+
+// The Gaussian of an emission spectrum (mean 0 = the reference wavelength)
+// and a check that every wavelength it can emit is > 0 nm and, when some
+// material has dispersion, gives every material an index > 0.
+lxo_status spectrum(lxo_ctx* c, float mean_nm, float fwhm_nm, const char* what, size_t idx, bool check_index,
+                    lxo::Spectrum* out)
+{
+    if (!std::isfinite(mean_nm) || !std::isfinite(fwhm_nm) || mean_nm < 0.0f || fwhm_nm < 0.0f)
+        return fail(c, LXO_ERR_ARG, "%s %zu: spectrum mean %g nm, FWHM %g nm (finite, >= 0)", what, idx, mean_nm,
+                    fwhm_nm);
+    const double mean = mean_nm > 0.0f ? (double)mean_nm : (double)LXO_REF_WAVELENGTH_NM;
+    const double sigma = (double)fwhm_nm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    const double lo = mean - kMaxDeviate * sigma, hi = mean + kMaxDeviate * sigma;
+    if (!(lo > 0.0))
+        return fail(c, LXO_ERR_ARG, "%s %zu: spectrum reaches %g nm", what, idx, lo);
+    if (check_index)
+        for (size_t m = 0; m < c->mats.size(); ++m) {
+            const lxo_material& x = c->mats[m];
+            const double r = (double)LXO_REF_WAVELENGTH_NM;
+            const double n_lo = x.n + x.dn_dlambda_per_nm * (lo - r), n_hi = x.n + x.dn_dlambda_per_nm * (hi - r);
+            if (!(n_lo > 0.0 && n_hi > 0.0))
+                return fail(c, LXO_ERR_ARG, "%s %zu: material %zu has n <= 0 within the spectrum (%g..%g nm)", what,
+                            idx, m, lo, hi);
+        }
+    if (out) *out = lxo::Spectrum{(float)mean, (float)sigma};
+    return LXO_OK;
+}
+
 lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, const lxo_run_params* rp,
                        lxo::PropParams* p)
 {
@@ -131,6 +162,10 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
         p->mat[m].abs_len = (x.abs_len_mm > 0.0f && std::isfinite(x.abs_len_mm)) ? x.abs_len_mm : INFINITY;
         p->mat[m].ray_len =
             (x.rayleigh_len_mm > 0.0f && std::isfinite(x.rayleigh_len_mm)) ? x.rayleigh_len_mm : INFINITY;
+        p->mat[m].dn = x.dn_dlambda_per_nm;
+        p->mat[m].dn_over_c = (float)((double)x.dn_dlambda_per_nm / 299.792458);
+        p->mat[m].ray_exp = x.rayleigh_exp;
+        if (x.dn_dlambda_per_nm != 0.0f || x.rayleigh_exp != 0.0f) p->spectral = 1;
     }
     for (int s = 0; s < S; ++s) {
         const lxo_surface& x = c->surfs[s];
@@ -156,6 +191,8 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
         return fail(c, LXO_ERR_ARG, "source time profile: singlet_frac %g not in [0, 1] or a negative constant",
                     src->singlet_frac);
     lxo::SourceDev& sd = p->src;
+    lxo_status st = spectrum(c, src->wl_mean_nm, src->wl_fwhm_nm, "source", 0, p->spectral != 0, &sd.spec);
+    if (st) return st;
     sd.kind = src->kind;
     sd.medium = src->medium;
     sd.n_sides = src->n_sides;
@@ -202,6 +239,10 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
     if (rp && (rp->flags & LXO_FLAG_ADJOINT)) {
         for (size_t i = 0; i < c->adj_mats.size(); ++i) {
             if (c->adj_mats[i] >= M) return fail(c, LXO_ERR_ARG, "adjoint material %d >= %d", c->adj_mats[i], M);
+            // the path-length tally serves L_abs and L_ray together, so a
+            // Rayleigh length that changes with the wavelength has no tally
+            if (c->mats[c->adj_mats[i]].rayleigh_exp != 0.0f)
+                return fail(c, LXO_ERR_ARG, "adjoint material %d has rayleigh_exp != 0", c->adj_mats[i]);
             p->adj_mat_slot[c->adj_mats[i]] = (signed char)i;
         }
         for (size_t j = 0; j < c->adj_surfs.size(); ++j) {
@@ -301,8 +342,10 @@ lxo_status lxo_set_materials(lxo_ctx* c, const lxo_material* m, uint32_t n)
     if (!m || n == 0 || n > LXO_MAX_MATERIALS)
         return fail(c, LXO_ERR_ARG, "set_materials: need 1..%d materials", LXO_MAX_MATERIALS);
     for (uint32_t i = 0; i < n; ++i)
-        if (!(m[i].n > 0.0f) || std::isnan(m[i].abs_len_mm) || std::isnan(m[i].rayleigh_len_mm))
-            return fail(c, LXO_ERR_ARG, "set_materials: material %u invalid (n must be > 0, lengths not NaN)", i);
+        if (!(m[i].n > 0.0f) || std::isnan(m[i].abs_len_mm) || std::isnan(m[i].rayleigh_len_mm) ||
+            !std::isfinite(m[i].dn_dlambda_per_nm) || !std::isfinite(m[i].rayleigh_exp))
+            return fail(c, LXO_ERR_ARG,
+                        "set_materials: material %u invalid (n must be > 0, lengths not NaN, dispersion finite)", i);
     c->mats.assign(m, m + n);
     c->validated = false;
     return LXO_OK;
@@ -432,7 +475,7 @@ lxo_status lxo_trace_rays(lxo_ctx* c, const float* org, const float* dir, const 
 }
 
 lxo_status lxo_sample_source(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, uint64_t seed,
-                             float* pos, float* dir, float* pol, float* time, void* stream)
+                             float* pos, float* dir, float* pol, float* time, float* wavelength, void* stream)
 {
     if (!c) return LXO_ERR_ARG;
     if (c->mats.empty()) return fail(c, LXO_ERR_STATE, "sample_source: no materials set");
@@ -443,7 +486,7 @@ lxo_status lxo_sample_source(lxo_ctx* c, const lxo_source* src, uint64_t n, uint
     lxo_status s = fill_params(c, src, n, base, &rp, &p);
     if (s) return s;
     DeviceGuard g(c->device);
-    CK(lxo::launch_sample_source(p, pos, dir, pol, time, (cudaStream_t)stream), "sample_source");
+    CK(lxo::launch_sample_source(p, pos, dir, pol, time, wavelength, (cudaStream_t)stream), "sample_source");
     return LXO_OK;
 }
 
@@ -540,8 +583,11 @@ lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n)
             !(x.tau_triplet_ns >= 0.0f))
             return fail(c, LXO_ERR_ARG, "upload_events: event %u time profile (f %g, tau %g, %g)", e, x.singlet_frac,
                         x.tau_singlet_ns, x.tau_triplet_ns);
+        lxo::Spectrum sp;
+        lxo_status st = spectrum(c, x.wl_mean_nm, x.wl_fwhm_nm, "upload_events: event", e, false, &sp);
+        if (st) return st;
         h[e] = lxo::EventDev{x.kind, x.medium, {x.center[0], x.center[1], x.center[2]}, {x.p1[0], x.p1[1], x.p1[2]},
-                             x.radius, x.t0, {x.singlet_frac, x.tau_singlet_ns, x.tau_triplet_ns}};
+                             x.radius, x.t0, {x.singlet_frac, x.tau_singlet_ns, x.tau_triplet_ns}, sp};
         pre[e + 1] = pre[e] + x.n_photons;
     }
     DeviceGuard g(c->device);
@@ -583,6 +629,12 @@ lxo_status lxo_propagate_events(lxo_ctx* c, const lxo_run_params* rp, const lxo_
     lxo::PropParams p;
     s = fill_params(c, &src, c->ev_total, 0, rp, &p);
     if (s) return s;
+    if (p.spectral)  // the materials may have changed since the upload
+        for (size_t e = 0; e < c->events.size(); ++e) {
+            s = spectrum(c, c->events[e].wl_mean_nm, c->events[e].wl_fwhm_nm, "propagate_events: event", e, true,
+                         nullptr);
+            if (s) return s;
+        }
     p.out = *out;
     p.n_events = (uint32_t)c->events.size();
     p.events = c->d_events;

@@ -81,6 +81,15 @@ struct DevMaterial {
     float n_over_c;   // ns per mm
     float abs_len;    // +inf = none
     float ray_len;    // +inf = none
+    float dn;         // dn / dlambda per nm about the reference wavelength
+    float dn_over_c;  // dn / c, ns per mm per nm
+    float ray_exp;    // Rayleigh length scales as (lambda / reference)^ray_exp
+};
+
+// Gaussian emission spectrum: mean and standard deviation in nm (sigma 0 =
+// one wavelength)
+struct Spectrum {
+    float mean, sigma;
 };
 
 struct DevSurface {
@@ -115,6 +124,7 @@ struct SourceDev {
     int kind, medium, n_sides;
     float radius, z_min, z_max, apothem, t0;
     TimeProfile prof;
+    Spectrum spec;
     float phase_turns;    // polygon phase / (2 pi)
     float center[3], p1[3];
     float side_cos[kMaxPolySides], side_sin[kMaxPolySides];
@@ -127,6 +137,7 @@ struct EventDev {
     int kind, medium;
     float center[3], p1[3], radius, t0;
     TimeProfile prof;
+    Spectrum spec;
 };
 
 struct PropParams {
@@ -135,6 +146,7 @@ struct PropParams {
     DevMaterial mat[LXO_MAX_MATERIALS];
     DevSurface surf[LXO_MAX_SURFACES];
     int n_mat, n_surf, n_chan, n_fates;
+    int spectral;                      // 1: some material has dispersion, photons carry a wavelength
     uint64_t n, base, seed;
     uint32_t max_steps, n_tbins, flags;
     float tbin;
@@ -155,7 +167,8 @@ struct PropParams {
 // kernel launchers (lxo_kernels.cu)
 cudaError_t launch_trace(const Scene& sc, const float* org, const float* dir, const uint32_t* skip,
                          const float* tmax, uint32_t n, uint32_t* hit, float* t, int* err, cudaStream_t st);
-cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, float* time, cudaStream_t st);
+cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, float* time,
+                                 float* wavelength, cudaStream_t st);
 cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st);
 
 struct AdjCoef {   // per parameter q: J[c][q] = a * sums[c][ia] + b * sums[c][ib]

@@ -407,6 +407,7 @@ __global__ void k_trace(const Scene sc, const float* __restrict__ org, const flo
 struct Photon {
     float3 pos, dir, pol;
     float time;
+    float wl;             // wavelength, nm (set only when some material has dispersion)
     int medium;
     uint32_t last;
     uint32_t step;
@@ -447,6 +448,32 @@ __device__ __forceinline__ float emission_delay(const PropParams& p, uint64_t pi
     return -tau * logf(u.u1);
 }
 
+// Wavelength from the Gaussian emission spectrum (Sec. 2.2, Table 2): the
+// Box-Muller transform of the last two uniforms of the emission draw.
+__device__ __forceinline__ float emission_wavelength(const PropParams& p, uint64_t pid, const Spectrum& sp)
+{
+    if (sp.sigma == 0.0f) return sp.mean;
+    const U4 u = draw4(p.seed, pid, kSourceStep, 0xFFFFFFFFu);
+    float s, c;
+    sincospif(2.0f * u.u3, &s, &c);
+    return fmaf(sp.sigma, sqrtf(-2.0f * logf(u.u2)) * c, sp.mean);
+}
+
+// Index and slowness (n / c) of a material at the photon's wavelength: the
+// table values unless some material has dispersion (the kSpectral build of
+// the propagation kernel, whose photons carry a wavelength).
+template <bool kSpectral>
+__device__ __forceinline__ float n_at(const DevMaterial& m, float wl)
+{
+    return kSpectral ? fmaf(m.dn, wl - LXO_REF_WAVELENGTH_NM, m.n) : m.n;
+}
+
+template <bool kSpectral>
+__device__ __forceinline__ float n_over_c_at(const DevMaterial& m, float wl)
+{
+    return kSpectral ? fmaf(m.dn_over_c, wl - LXO_REF_WAVELENGTH_NM, m.n_over_c) : m.n_over_c;
+}
+
 __device__ Photon make_event_photon(const PropParams& p, uint64_t idx)
 {
     uint32_t lo = 0, hi = p.n_events;  // find e with prefix[e] <= idx < prefix[e+1]
@@ -459,6 +486,7 @@ __device__ Photon make_event_photon(const PropParams& p, uint64_t idx)
     ph.pid = ((uint64_t)lo << 32) | (uint64_t)(idx - __ldg(&p.ev_prefix[lo]));
     ph.medium = ev.medium;
     ph.time = ev.t0 + emission_delay(p, ph.pid, ev.prof);
+    ph.wl = p.spectral ? emission_wavelength(p, ph.pid, ev.spec) : 0.0f;
     ph.last = LXO_NO_HIT;
     ph.step = 0;
     const U4 u = draw4(p.seed, ph.pid, kSourceStep, 0);
@@ -495,6 +523,7 @@ __device__ Photon make_photon(const PropParams& p, uint64_t idx)
     ph.pid = p.base + idx;
     ph.medium = s.medium;
     ph.time = s.t0 + emission_delay(p, ph.pid, s.prof);
+    ph.wl = p.spectral ? emission_wavelength(p, ph.pid, s.spec) : 0.0f;
     ph.last = LXO_NO_HIT;
     ph.step = 0;
     if (s.kind == LXO_SRC_EXPLICIT) {
@@ -550,7 +579,7 @@ __device__ Photon make_photon(const PropParams& p, uint64_t idx)
 }
 
 __global__ void k_sample_source(const __grid_constant__ PropParams p, float* pos, float* dir, float* pol,
-                                float* time)
+                                float* time, float* wavelength)
 {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n) return;
@@ -559,6 +588,7 @@ __global__ void k_sample_source(const __grid_constant__ PropParams p, float* pos
     dir[3 * i] = ph.dir.x; dir[3 * i + 1] = ph.dir.y; dir[3 * i + 2] = ph.dir.z;
     pol[3 * i] = ph.pol.x; pol[3 * i + 1] = ph.pol.y; pol[3 * i + 2] = ph.pol.z;
     if (time) time[i] = ph.time;
+    if (wavelength) wavelength[i] = emission_wavelength(p, ph.pid, p.src.spec);
 }
 
 // ---------------------------------------------------------------------------
@@ -671,13 +701,20 @@ struct StepDraw {
     float d_abs, d_ray, u2, u3;
 };
 
+template <bool kSpectral>
 __device__ __forceinline__ StepDraw begin_step(const PropParams& p, const Photon& ph)
 {
     const U4 u = draw4(p.seed, ph.pid, ph.step, 0);
     const DevMaterial& mt = p.mat[ph.medium];
     StepDraw sd;
+    float ray_len = mt.ray_len;
+    // (lambda / reference)^p as 2^(p log2(lambda / reference)), with the fast
+    // base-2 logarithm (documented error: 2^-22 absolute on [0.5, 2], 2 ulp
+    // elsewhere) in place of powf's exact-case handling
+    if (kSpectral && mt.ray_exp != 0.0f)
+        ray_len *= exp2f(mt.ray_exp * __log2f(ph.wl * (1.0f / LXO_REF_WAVELENGTH_NM)));
     sd.d_abs = isinf(mt.abs_len) ? INFINITY : -mt.abs_len * logf(u.u0);
-    sd.d_ray = isinf(mt.ray_len) ? INFINITY : -mt.ray_len * logf(u.u1);
+    sd.d_ray = isinf(ray_len) ? INFINITY : -ray_len * logf(u.u1);
     sd.u2 = u.u2;
     sd.u3 = u.u3;
     return sd;
@@ -698,7 +735,7 @@ __device__ __forceinline__ void step_histogram(const PropParams& p, const Photon
 // Adjoint tallies of one lane live in shared memory, tally k at tl[k * kPropThreads].
 constexpr int kAdjMaxK = 2 * (LXO_ADJ_MAX_MATERIALS + LXO_ADJ_MAX_SURFACES);
 
-template <bool kAdjoint>
+template <bool kAdjoint, bool kSpectral>
 __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, const Hit& h, int& detail,
                            float* tl)
 {
@@ -712,7 +749,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
             return LXO_FATE_ESCAPED;
         }
         ph.pos = ph.pos + d_int * ph.dir;
-        ph.time += d_int * mt.n_over_c;
+        ph.time += d_int * n_over_c_at<kSpectral>(mt, ph.wl);
         if (kAdjoint && ms >= 0) tl[(2 * ms) * kPropThreadsK] += d_int;
         if (d_abs <= d_ray) {
             detail = ph.medium;
@@ -725,7 +762,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
     }
     const float3 o_ray = ph.pos;
     ph.pos = ph.pos + h.t * ph.dir;
-    ph.time += h.t * mt.n_over_c;
+    ph.time += h.t * n_over_c_at<kSpectral>(mt, ph.wl);
     if (kAdjoint && ms >= 0) tl[(2 * ms) * kPropThreadsK] += h.t;
     // geometric normal and attributes of the triangle hit (record in leaf order)
     if (LXO_CHECK_BOUNDS && h.rec >= p.sc.n_records) {
@@ -750,7 +787,8 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
             detail = (int)h.id;
             return LXO_FATE_GEOM_ERR;
         }
-        const bool refl = dielectric(ph, Nf, p.mat[from].n, p.mat[to].n, u.u2);
+        const bool refl = dielectric(ph, Nf, n_at<kSpectral>(p.mat[from], ph.wl), n_at<kSpectral>(p.mat[to], ph.wl),
+                                      u.u2);
         if (!refl) ph.medium = to;
         spawn_offset(ph, o_ray, h.t, Nf, refl ? 1.0f : -1.0f);
         return -1;
@@ -810,10 +848,10 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
 }
 
 // one whole interaction (draw, closest hit, interaction)
-template <bool kStats, bool kAdjoint>
+template <bool kStats, bool kAdjoint, bool kSpectral>
 __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counters& cnt, float* tl)
 {
-    const StepDraw sd = begin_step(p, ph);
+    const StepDraw sd = begin_step<kSpectral>(p, ph);
     const long long c0 = kStats ? clock64() : 0;
     const uint32_t n0 = kStats ? cnt.nodes : 0, l0 = kStats ? cnt.leaves : 0;
     const Hit h = closest_hit<kStats>(p.sc, ph.pos, ph.dir, ph.last, fminf(sd.d_abs, sd.d_ray), p.err, cnt);
@@ -821,7 +859,7 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
         cnt.trav_cycles += (unsigned long long)(clock64() - c0);
         step_histogram<kStats>(p, ph, cnt.nodes - n0, cnt.leaves - l0);
     }
-    return finish_step<kAdjoint>(p, ph, sd, h, detail, tl);
+    return finish_step<kAdjoint, kSpectral>(p, ph, sd, h, detail, tl);
 }
 
 // ---------------------------------------------------------------------------
@@ -887,7 +925,7 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
 // from a warp-local chunk (ballot + prefix popcount), chunks of p.chunk ids
 // coming from the global work-queue head.  Source sampling and tallies thus
 // run on many lanes at once instead of one lane per iteration.
-template <bool kStats, bool kAdjoint>
+template <bool kStats, bool kAdjoint, bool kSpectral>
 __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(const __grid_constant__ PropParams p)
 {
     Counters cnt{};
@@ -944,7 +982,7 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
         if (kStats && lane == 0) outer_iters++;
         const long long c0 = kStats ? clock64() : 0;
         if (alive) {
-            fate = photon_step<kStats, kAdjoint>(p, ph, detail, cnt, tl);
+            fate = photon_step<kStats, kAdjoint, kSpectral>(p, ph, detail, cnt, tl);
             ph.step++;
             if (kStats) my_steps++;
             if (fate < 0 && ph.step >= p.max_steps) fate = LXO_FATE_TRUNCATED;
@@ -984,12 +1022,12 @@ cudaError_t launch_trace(const Scene& sc, const float* org, const float* dir, co
 }
 
 cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, float* pol, float* time,
-                                 cudaStream_t st)
+                                 float* wavelength, cudaStream_t st)
 {
     if (p.n == 0) return cudaSuccess;
     const int threads = 128;
     const uint64_t blocks = (p.n + threads - 1) / threads;
-    k_sample_source<<<(unsigned)blocks, threads, 0, st>>>(p, pos, dir, pol, time);
+    k_sample_source<<<(unsigned)blocks, threads, 0, st>>>(p, pos, dir, pol, time, wavelength);
     return cudaGetLastError();
 }
 
@@ -1001,8 +1039,10 @@ cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const bool stats = (p.flags & LXO_FLAG_STATS) != 0;
     const bool adj = (p.flags & LXO_FLAG_ADJOINT) != 0;
-    auto kern = stats ? (adj ? k_propagate<true, true> : k_propagate<true, false>)
-                      : (adj ? k_propagate<false, true> : k_propagate<false, false>);
+    auto kern = p.spectral ? (stats ? (adj ? k_propagate<true, true, true> : k_propagate<true, false, true>)
+                                    : (adj ? k_propagate<false, true, true> : k_propagate<false, false, true>))
+                           : (stats ? (adj ? k_propagate<true, true, false> : k_propagate<true, false, false>)
+                                    : (adj ? k_propagate<false, true, false> : k_propagate<false, false, false>));
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPropThreads, 0);
     if (e != cudaSuccess) return e;
     if (p.blocks_per_sm > 0 && (int)p.blocks_per_sm < per_sm) per_sm = (int)p.blocks_per_sm;

@@ -56,10 +56,16 @@ INF = float("inf")
 
 @dataclass
 class Material:
+    """Optical constants at 175 nm (the paper's Table 2).  A photon of
+    wavelength wl (nm) sees the index n + dn_dlambda_per_nm * (wl - 175) and
+    the Rayleigh length rayleigh_len_mm * (wl / 175) ** rayleigh_exp; the
+    paper uses the 175 nm values for every photon (both 0)."""
     name: str
     n: float
     abs_len_mm: float = INF
     rayleigh_len_mm: float = INF
+    dn_dlambda_per_nm: float = 0.0
+    rayleigh_exp: float = 0.0
 
 
 @dataclass
@@ -93,6 +99,16 @@ class Source:
     singlet_frac: float = 0.0
     tau_singlet_ns: float = 0.0
     tau_triplet_ns: float = 0.0
+    # Gaussian emission spectrum: mean (0 = 175 nm) and full width at half
+    # maximum (0 = one wavelength), nm
+    wl_mean_nm: float = 0.0
+    wl_fwhm_nm: float = 0.0
+
+    def with_spectrum(self, spectrum):
+        """This source with a Gaussian emission spectrum (mean_nm, fwhm_nm),
+        e.g. LXE_SPECTRUM."""
+        from dataclasses import replace
+        return replace(self, wl_mean_nm=spectrum[0], wl_fwhm_nm=spectrum[1])
 
     def with_profile(self, profile):
         """This source with a scintillation time profile (singlet_frac,
@@ -106,6 +122,8 @@ class Source:
 # electronic recoils
 NR_PROFILE = (0.66, 3.5, 24.0)
 ER_PROFILE = (0.22, 3.5, 24.0)
+# LXe scintillation spectrum (Sec. 2.2, Table 2): Gaussian, mean and FWHM in nm
+LXE_SPECTRUM = (174.8, 10.2)
 
 
 @dataclass

@@ -37,6 +37,7 @@ def make_source(src: Source, explicit=None) -> A.lxo_source:
     s.t0 = float(src.t0)
     s.singlet_frac, s.tau_singlet_ns, s.tau_triplet_ns = (float(src.singlet_frac), float(src.tau_singlet_ns),
                                                           float(src.tau_triplet_ns))
+    s.wl_mean_nm, s.wl_fwhm_nm = float(src.wl_mean_nm), float(src.wl_fwhm_nm)
     if explicit is not None:
         pos, dir, pol = explicit
         s.pos, s.dir, s.pol = pos.data_ptr(), dir.data_ptr(), pol.data_ptr()
@@ -105,6 +106,8 @@ class Tracker:
             # passed as given: inf means no process, NaN is rejected by the library
             arr[i].abs_len_mm = m.abs_len_mm
             arr[i].rayleigh_len_mm = m.rayleigh_len_mm
+            arr[i].dn_dlambda_per_nm = m.dn_dlambda_per_nm
+            arr[i].rayleigh_exp = m.rayleigh_exp
         self._check(self._L.lxo_set_materials(self._ctx, arr, len(mats)))
         self.n_materials = len(mats)
 
@@ -194,16 +197,18 @@ class Tracker:
                                            _ptr(t), _stream(stream)))
         return hit, t
 
-    def sample_source(self, n, base=0, seed=0, source=None, stream=None, time=False):
-        """First photon states (pos, dir, pol [n, 3]; and emission times [n] if time)."""
+    def sample_source(self, n, base=0, seed=0, source=None, stream=None, time=False, wavelength=False):
+        """First photon states: pos, dir, pol [n, 3]; then the emission times
+        [n] if time, and the wavelengths [n] (nm) if wavelength."""
         src = make_source(source or self.det.source)
         pos = torch.empty((n, 3), dtype=torch.float32, device=self.device)
         dir = torch.empty_like(pos)
         pol = torch.empty_like(pos)
         t = torch.empty(n, dtype=torch.float32, device=self.device) if time else None
+        wl = torch.empty(n, dtype=torch.float32, device=self.device) if wavelength else None
         self._check(self._L.lxo_sample_source(self._ctx, C.byref(src), n, base, seed, _ptr(pos), _ptr(dir), _ptr(pol),
-                                              _ptr(t), _stream(stream)))
-        return (pos, dir, pol, t) if time else (pos, dir, pol)
+                                              _ptr(t), _ptr(wl), _stream(stream)))
+        return (pos, dir, pol) + ((t,) if time else ()) + ((wl,) if wavelength else ())
 
     # -- propagation --------------------------------------------------------
     def alloc_results(self, n_tbins=1000, per_photon_n=0):
@@ -286,6 +291,7 @@ class Tracker:
             e.radius, e.t0, e.n_photons = float(src.radius), float(src.t0), int(n)
             e.singlet_frac, e.tau_singlet_ns, e.tau_triplet_ns = (float(src.singlet_frac), float(src.tau_singlet_ns),
                                                                   float(src.tau_triplet_ns))
+            e.wl_mean_nm, e.wl_fwhm_nm = float(src.wl_mean_nm), float(src.wl_fwhm_nm)
         self._check(self._L.lxo_upload_events(self._ctx, arr, len(events)))
         self.n_events = len(events)
         self.event_photons = int(sum(int(n) for _, n in events))

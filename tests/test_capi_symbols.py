@@ -50,3 +50,28 @@ def test_checked_build_compiles_and_exports_every_symbol():
     lib = ctypes.CDLL(path)
     for n in sorted(declared_symbols()):
         assert hasattr(lib, n), n
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct of the binding has the size and field offsets that a C
+    compiler gives the declaration in include/lxo.h."""
+    import subprocess
+    structs = [c for c in vars(_capi).values()
+               if isinstance(c, type) and issubclass(c, ctypes.Structure) and c.__name__.startswith("lxo_")]
+    assert {"lxo_material", "lxo_source", "lxo_event", "lxo_results", "lxo_run_params"} <= {c.__name__ for c in structs}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lxo.h"', "int main(void) {"]
+    for c in structs:
+        lines.append(f'printf("{c.__name__} size %zu\\n", sizeof({c.__name__}));')
+        for f in c._fields_:
+            lines.append(f'printf("{c.__name__} {f[0]} %zu\\n", offsetof({c.__name__}, {f[0]}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for c in structs:
+        assert int(got[f"{c.__name__} size"]) == ctypes.sizeof(c), c.__name__
+        for f in c._fields_:
+            assert int(got[f"{c.__name__} {f[0]}"]) == getattr(c, f[0]).offset, (c.__name__, f[0])
