@@ -275,6 +275,29 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
         z_sum.append(float((t2.sum() - mean) / sd) if n else None)
     out["per_pmt"] = {"sum_t2": sum_t2, "pmts": n_pmt, "expected": [k * nu / (nu - 2) for k in n_pmt],
                       "z": z_sum}
+    # rings: PMTs of one array at the same hexagonal ring (radius / pitch,
+    # rounded), the aggregate between one array and one PMT
+    pos = np.asarray(trk.det.pmt_pos, np.float64)[:, :2]
+    r = np.hypot(pos[:, 0], pos[:, 1])
+    d = np.sqrt(((pos[:, None] - pos[None]) ** 2).sum(-1)) + np.eye(len(pos)) * 1e9
+    pitch = float(np.median(d.min(1)))
+    ring = np.rint(r / pitch).astype(int)
+    arr = np.asarray(trk.det.pmt_array)
+    labels, rings_out = [], {"adjoint": [], "fd": [], "rel_diff": [], "z": []}
+    for a_ in (1, 0):
+        for k in np.unique(ring[arr == a_]):
+            m = (arr == a_) & (ring == k)
+            av, fv = adj_pmt[:, m].sum(1), fd_pmt[:, m].sum(1)  # [batches, Q]
+            am, fm = av.mean(0), fv.mean(0)
+            sa, sf = av.std(0, ddof=1) / math.sqrt(batches), fv.std(0, ddof=1) / math.sqrt(batches)
+            labels.append(f"{'top' if a_ == 1 else 'bottom'} ring {k} ({int(m.sum())} PMTs)")
+            rings_out["adjoint"].append(am.tolist())
+            rings_out["fd"].append(fm.tolist())
+            rings_out["rel_diff"].append((np.abs(am - fm) / np.abs(fm)).tolist())
+            rings_out["z"].append((np.abs(am - fm) / np.sqrt(sa ** 2 + sf ** 2)).tolist())
+    zr = np.array(rings_out["z"])
+    out["rings"] = {"labels": labels, "pitch_mm": pitch, **rings_out, "z_max": zr.max(0).tolist(),
+                    "n_over_2": (zr > 2).sum(0).tolist()}
     if wide:
         out["wide_step"] = {"h_rel": h_wide, "params": [names[q] for q in wide]}
         for a, name in enumerate(aggs):

@@ -396,16 +396,27 @@ def hex_lattice(pitch, extent):
 # ----------------------------------------------------------------------------
 # detector parts
 # ----------------------------------------------------------------------------
-def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_plate, subdivide=False, holes=True):
+def hex_ring(centres, pitch):
+    """Hexagonal ring of hex_lattice sites: the fewest neighbour steps from
+    the site at the origin (0 for the centre, 1 for its 6 neighbours, ...)."""
+    b = np.rint(centres[:, 1] / (pitch * math.sqrt(3) / 2))
+    a = np.rint((centres[:, 0] - 0.5 * pitch * b) / pitch)
+    return ((np.abs(a) + np.abs(b) + np.abs(a + b)) / 2).astype(int)
+
+
+def _pmt_plate(b, wall2, z_plate, pitch, r_window, k_seg, facing, mat_xe, surf_plate, subdivide=False, holes=True,
+               max_ring=None):
     """PTFE plate at ``z_plate`` filling the wall polygon, with a circular hole
     of radius ``r_window`` at every hex-lattice site whose window fits inside
-    the wall (no holes if not ``holes``).  ``facing`` = +1 if the plate faces
-    up (bottom array), -1 if it faces down (top array).  Returns the PMT
-    centres (x, y)."""
+    the wall (no holes if not ``holes``; only sites of hexagonal ring <=
+    ``max_ring`` if given).  ``facing`` = +1 if the plate faces up (bottom
+    array), -1 if it faces down (top array).  Returns the PMT centres (x, y)."""
     extent = np.abs(wall2).max() + pitch
     centres = hex_lattice(pitch, extent)
     # a PMT sits on every site whose window circle is inside the wall (0.5 mm clearance)
     has_pmt = _inside_convex(centres, wall2, margin=r_window + 0.5) & holes
+    if max_ring is not None:
+        has_pmt &= hex_ring(centres, pitch) <= max_ring
     hexagon = polygon_vertices(6, pitch / math.sqrt(3), math.pi / 6)  # flat-to-flat = pitch
     pmts, cells = [], []
     normal = (0.0, 0.0, -float(facing))  # plate normal points from Xe into PTFE
@@ -872,8 +883,9 @@ def scaled_tpc(r_ptfe_lxe=0.95, r_ptfe_gxe=0.70, qe=0.3, lxe_abs_mm=50_000.0, lx
     ]
     wall2 = polygon_vertices(64, R)
     b = _Builder()
-    bot, bot_edge = _pmt_plate(b, wall2, z_bot, pitch, r_w, k_seg, +1, LXE, S_PTFE_L)
-    top, top_edge = _pmt_plate(b, wall2, z_top, pitch, r_w, k_seg, -1, GXE, S_PTFE_G)
+    # 61 windows per array: hexagonal rings 0..4 (1 + 6 + 12 + 18 + 24)
+    bot, bot_edge = _pmt_plate(b, wall2, z_bot, pitch, r_w, k_seg, +1, LXE, S_PTFE_L, max_ring=4)
+    top, top_edge = _pmt_plate(b, wall2, z_top, pitch, r_w, k_seg, -1, GXE, S_PTFE_G, max_ring=4)
     # the wall is split at every electrode plane so the disk rims weld to it
     _wall(b, wall2, z_bot, -495.0, LXE, S_PTFE_L, bottom_pts=bot_edge)
     _wall(b, wall2, -495.0, -5.0, LXE, S_PTFE_L)

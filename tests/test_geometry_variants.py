@@ -152,3 +152,20 @@ def test_map_summary_reads_the_features():
     assert s["radial_spread_mid_z"] == pytest.approx(0.0)
     assert s["bottom_edge_minus_bottom_centre"] == pytest.approx(-7.0)
     assert s["t90_near_bottom"] == pytest.approx(90.0) and s["t90_near_top"] == pytest.approx(150.0)
+
+
+def test_scaled_tpc_has_61_plus_61_windows_in_five_hexagonal_rings():
+    """The 50 cm TPC of the adjoint workload: 61 windows per array, the
+    hexagonal rings 0..4 of the 80 mm lattice (ring k holds 6k sites)."""
+    c = g.hex_lattice(80.0, 700.0)
+    r = g.hex_ring(c, 80.0)
+    assert [int((r == k).sum()) for k in range(6)] == [1, 6, 12, 18, 24, 30]
+    # ring k sites lie between k * pitch * sqrt(3)/2 and k * pitch from the centre
+    d = np.hypot(c[:, 0], c[:, 1])
+    for k in range(1, 6):
+        assert np.all(d[r == k] >= k * 80.0 * np.sqrt(3) / 2 - 1e-6) and np.all(d[r == k] <= k * 80.0 + 1e-6)
+    det = g.scaled_tpc()
+    assert det.n_pmts == 122 and np.bincount(det.pmt_array).tolist() == [61, 61]
+    top = det.pmt_pos[det.pmt_array == 1][:, :2]
+    assert np.allclose(np.sort(top, axis=0), np.sort(det.pmt_pos[det.pmt_array == 0][:, :2], axis=0))
+    assert np.hypot(top[:, 0], top[:, 1]).max() == pytest.approx(320.0)
