@@ -190,6 +190,26 @@ def adjoint_cost(args, n=10_000_000, reps=3):
     return res
 
 
+def pmt_rings(det):
+    """PMTs grouped by array (top first) and hexagonal ring of the window
+    lattice (pitch = nearest-neighbour distance within one array).  Returns
+    labels, boolean masks [P] and the pitch."""
+    from paper_2203_14354_gb300 import geometry
+    pos = np.asarray(det.pmt_pos, np.float64)[:, :2]
+    arr = np.asarray(det.pmt_array)
+    one = pos[arr == arr[0]]
+    d = np.sqrt(((one[:, None] - one[None]) ** 2).sum(-1)) + np.eye(len(one)) * 1e30
+    pitch = float(np.median(d.min(1)))
+    ring = geometry.hex_ring(pos, pitch)
+    labels, masks = [], []
+    for a in (1, 0):
+        for k in np.unique(ring[arr == a]):
+            m = (arr == a) & (ring == k)
+            labels.append(f"{'top' if a == 1 else 'bottom'} ring {k} ({int(m.sum())} PMTs)")
+            masks.append(m)
+    return labels, masks, pitch
+
+
 def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wide=3e-2, noisy=0.02):
     """Accuracy of the adjoint gradient of detected hits (total, top array,
     bottom array) against central finite differences with common random
@@ -277,24 +297,16 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
                       "z": z_sum}
     # rings: PMTs of one array at the same hexagonal ring (radius / pitch,
     # rounded), the aggregate between one array and one PMT
-    pos = np.asarray(trk.det.pmt_pos, np.float64)[:, :2]
-    r = np.hypot(pos[:, 0], pos[:, 1])
-    d = np.sqrt(((pos[:, None] - pos[None]) ** 2).sum(-1)) + np.eye(len(pos)) * 1e9
-    pitch = float(np.median(d.min(1)))
-    ring = np.rint(r / pitch).astype(int)
-    arr = np.asarray(trk.det.pmt_array)
-    labels, rings_out = [], {"adjoint": [], "fd": [], "rel_diff": [], "z": []}
-    for a_ in (1, 0):
-        for k in np.unique(ring[arr == a_]):
-            m = (arr == a_) & (ring == k)
-            av, fv = adj_pmt[:, m].sum(1), fd_pmt[:, m].sum(1)  # [batches, Q]
-            am, fm = av.mean(0), fv.mean(0)
-            sa, sf = av.std(0, ddof=1) / math.sqrt(batches), fv.std(0, ddof=1) / math.sqrt(batches)
-            labels.append(f"{'top' if a_ == 1 else 'bottom'} ring {k} ({int(m.sum())} PMTs)")
-            rings_out["adjoint"].append(am.tolist())
-            rings_out["fd"].append(fm.tolist())
-            rings_out["rel_diff"].append((np.abs(am - fm) / np.abs(fm)).tolist())
-            rings_out["z"].append((np.abs(am - fm) / np.sqrt(sa ** 2 + sf ** 2)).tolist())
+    labels, masks, pitch = pmt_rings(trk.det)
+    rings_out = {"adjoint": [], "fd": [], "rel_diff": [], "z": []}
+    for m in masks:
+        av, fv = adj_pmt[:, m].sum(1), fd_pmt[:, m].sum(1)  # [batches, Q]
+        am, fm = av.mean(0), fv.mean(0)
+        sa, sf = av.std(0, ddof=1) / math.sqrt(batches), fv.std(0, ddof=1) / math.sqrt(batches)
+        rings_out["adjoint"].append(am.tolist())
+        rings_out["fd"].append(fm.tolist())
+        rings_out["rel_diff"].append((np.abs(am - fm) / np.abs(fm)).tolist())
+        rings_out["z"].append((np.abs(am - fm) / np.sqrt(sa ** 2 + sf ** 2)).tolist())
     zr = np.array(rings_out["z"])
     out["rings"] = {"labels": labels, "pitch_mm": pitch, **rings_out, "z_max": zr.max(0).tolist(),
                     "n_over_2": (zr > 2).sum(0).tolist()}

@@ -59,3 +59,17 @@ def test_reference_arm_line(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(a, 1, 2)
     assert buf.getvalue() == ""
+
+
+def test_pmt_rings_of_the_50cm_tpc():
+    """The ring aggregates of the adjoint check: per array, the hexagonal
+    rings 0..4 of the 80 mm window lattice, 1 + 6 + 12 + 18 + 24 windows."""
+    import bench
+    from paper_2203_14354_gb300 import geometry as g
+    labels, masks, pitch = bench.pmt_rings(g.scaled_tpc())
+    assert pitch == 80.0
+    assert [int(m.sum()) for m in masks] == [1, 6, 12, 18, 24] * 2
+    assert labels[0].startswith("top ring 0") and labels[5].startswith("bottom ring 0")
+    import numpy as np
+    together = np.sum(masks, axis=0)
+    assert np.all(together == 1)

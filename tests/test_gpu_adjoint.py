@@ -80,23 +80,38 @@ def scaled(T):
 
 
 def test_gpu_adjoint_matches_oracle(scaled):
+    """GPU and oracle Jacobians of the same photon ids agree statistically:
+    per aggregate (top, bottom, all) and parameter, the summed difference of
+    10 batches lies within 4 batch-means standard errors (the photons are
+    independent, so the batch differences are too); and within 10 %."""
     det, trk, orc = scaled
-    n = 200_000
-    out = trk.propagate(n, seed=3, adjoint=True)
-    sums_g = out["adjoint"].cpu().numpy()
-    J_g = trk.jacobian(out["adjoint"]).cpu().numpy()
-    ref = orc.propagate(n, seed=3, adjoint=True)
-    J_o = orc.jacobian(ref["adjoint"])
-    # the GPU Jacobian of the oracle's sums equals the oracle's Jacobian (same formula)
-    J_go = trk.jacobian(torch.from_numpy(ref["adjoint"]).cuda()).cpu().numpy()
-    np.testing.assert_allclose(J_go, J_o, rtol=1e-9, atol=1e-9)
-    # statistical parity of the tallies: totals and per array, per parameter
+    nb, m = 10, 20_000
     top = det.pmt_array == 1
-    for sel in (top, ~top, np.ones_like(top)):
-        a, b = J_g[sel].sum(0), J_o[sel].sum(0)
-        assert np.all(np.abs(a - b) <= 0.05 * np.abs(b) + 1e-6 * np.abs(J_o).max()), (a, b)
+    sels = (top, ~top, np.ones_like(top))
+    d = np.zeros((len(sels), nb, trk.n_params))
+    ref_tot = np.zeros((len(sels), trk.n_params))
+    sums_g, sums_o = 0.0, 0.0
+    for b in range(nb):
+        out = trk.propagate(m, base=b * m, seed=3, adjoint=True)
+        J_g = trk.jacobian(out["adjoint"]).cpu().numpy()
+        ref = orc.propagate(m, base=b * m, seed=3, adjoint=True)
+        J_o = orc.jacobian(ref["adjoint"])
+        if b == 0:
+            # the GPU Jacobian of the oracle's sums equals the oracle's Jacobian (same formula)
+            J_go = trk.jacobian(torch.from_numpy(ref["adjoint"]).cuda()).cpu().numpy()
+            np.testing.assert_allclose(J_go, J_o, rtol=1e-9, atol=1e-9)
+        for k, sel in enumerate(sels):
+            d[k, b] = J_g[sel].sum(0) - J_o[sel].sum(0)
+            ref_tot[k] += J_o[sel].sum(0)
+        sums_g = sums_g + out["adjoint"].cpu().numpy().sum(0)
+        sums_o = sums_o + ref["adjoint"].sum(0)
+    D = d.sum(1)
+    se = np.sqrt(nb) * d.std(1, ddof=1)
+    tiny = 1e-9 * np.abs(ref_tot).max()
+    assert np.all(np.abs(D) <= 4 * se + tiny), (D, se)
+    assert np.all(np.abs(D) <= 0.10 * np.abs(ref_tot) + tiny), (D, ref_tot)
     # the tallies themselves (path lengths, counts) agree per channel in sum
-    np.testing.assert_allclose(sums_g.sum(0), ref["adjoint"].sum(0), rtol=0.03)
+    np.testing.assert_allclose(sums_g, sums_o, rtol=0.03)
 
 
 def test_gpu_adjoint_vs_central_fd_crn(scaled):
