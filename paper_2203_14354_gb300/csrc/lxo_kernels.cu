@@ -866,7 +866,6 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
 // persistent propagation kernel
 // ---------------------------------------------------------------------------
 constexpr int kPropThreads = kPropThreadsK;
-constexpr uint32_t kChunkDefault = 64;
 // tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
 // idle; 5 CTAs of 256 threads per SM (48 registers) hide more L1/L2 latency
 // than 3 CTAs at 80 registers (+22 %) despite a few spills
