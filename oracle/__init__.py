@@ -41,9 +41,12 @@ class _Results(C.Structure):
 
 
 def lib():
+    """The oracle library: built from oracle.c, or the prebuilt library named
+    by the ORACLE_LIB environment variable (the mutation tests load copies
+    of oracle.c with one planted mistake this way)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         L.orc_scene_new.restype = C.c_void_p
         L.orc_scene_new.argtypes = [f32p, C.c_uint32, u32p, C.c_uint32, u8p, u8p, u16p, i32p]

@@ -18,11 +18,17 @@ def build(force=False):
         return OUT
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
     tmp = OUT + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-Wall", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-pthread", src, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    compile_library(src, tmp)
     os.replace(tmp, OUT)
     return OUT
+
+
+def compile_library(src, out):
+    """gcc with the oracle's flags: one C file (next to its oracle.h) to a
+    shared library."""
+    cmd = ["gcc", "-O2", "-std=c99", "-Wall", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-pthread", src, "-o", out, "-lm"]
+    subprocess.run(cmd, check=True)
 
 
 if __name__ == "__main__":

@@ -1,0 +1,105 @@
+"""Mutation tests of the oracle's pins.
+
+Each entry plants one plausible mistake in a copy of oracle.c: a dropped
+term, a wrong sign, a wrong index or a swapped operand. The copy is built
+with the oracle's own flags, and the pins named beside the mistake are run
+against it in a subprocess (ORACLE_LIB selects the library). At least one
+of them must fail. The unmodified oracle passes every pin (the rest of the
+suite), so a surviving mutant would mark a part of the oracle that no pin
+fixes."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = "tests/test_oracle_pins.py::"
+ADJ = "tests/test_oracle_adjoint.py::"
+TIME = "tests/test_oracle_time_profile.py::"
+SPEC = "tests/test_oracle_spectrum.py::"
+
+# (name, text in oracle.c, planted replacement, pins that must catch it)
+MUTANTS = [
+    ("Philox multiplier off by two", "uint64_t p0 = (uint64_t)0xD2511F53u * c0;",
+     "uint64_t p0 = (uint64_t)0xD2511F55u * c0;", [PINS + "test_philox_known_answers"]),
+    ("Fresnel r_p numerator with the indices swapped", "out[1] = (n2 * cos_i - n1 * cos_t)",
+     "out[1] = (n1 * cos_i - n2 * cos_t)", [PINS + "test_brewster_and_critical_angles"]),
+    ("Fresnel t_s over the p denominator", "out[2] = 2.0 * n1 * cos_i / (n1 * cos_i + n2 * cos_t);",
+     "out[2] = 2.0 * n1 * cos_i / (n2 * cos_i + n1 * cos_t);", [PINS + "test_fresnel_energy_conservation_and_stokes"]),
+    ("refracted direction with the wrong sign of cos t", "k_out[a] = eta * k[a] + (eta * cos_i - cos_t) * N[a];",
+     "k_out[a] = eta * k[a] + (eta * cos_i + cos_t) * N[a];", [PINS + "test_dielectric_geometry_and_polarisation"]),
+    ("s and p reflectances swapped in P(reflect)",
+     "double pr = tir ? 1.0 : cs * cs * f[0] * f[0] + cp * cp * f[1] * f[1];",
+     "double pr = tir ? 1.0 : cs * cs * f[1] * f[1] + cp * cp * f[0] * f[0];",
+     [PINS + "test_dielectric_geometry_and_polarisation", PINS + "test_brewster_reflection_is_s_polarised"]),
+    ("Rayleigh acceptance cos^2 instead of sin^2", "if (!(u[2] < 1.0 - ce * ce)) continue;",
+     "if (!(u[2] < ce * ce)) continue;", [PINS + "test_rayleigh_dipole_laws"]),
+    ("Rayleigh polarisation not projected off the new direction",
+     "double e[3] = {eps[0] - ce * kk[0], eps[1] - ce * kk[1], eps[2] - ce * kk[2]};",
+     "double e[3] = {eps[0], eps[1], eps[2]};", [PINS + "test_rayleigh_dipole_laws"]),
+    ("Lambert cos theta uniform instead of sqrt(u)", "double c = sqrt(u[0]), sn", "double c = u[0], sn",
+     [PINS + "test_lambert_cosine_law"]),
+    ("absorption distance drawn from the Rayleigh uniform",
+     "double d_abs = isinf(mat[1]) ? INFINITY : -mat[1] * log(u[0]);",
+     "double d_abs = isinf(mat[1]) ? INFINITY : -mat[1] * log(u[1]);",
+     [PINS + "test_competing_absorption_and_rayleigh"]),
+    ("speed c n instead of c / n", "double vel = C_MM_PER_NS / index_at(mat, wl);",
+     "double vel = C_MM_PER_NS * index_at(mat, wl);", [PINS + "test_rayleigh_mean_free_path_and_time"]),
+    ("reflector absorbs the reflected share", "if (!(u[2] < sp[0])) { fate = ORC_SURF_ABS",
+     "if (u[2] < sp[0]) { fate = ORC_SURF_ABS", [PINS + "test_reflector_absorption_geometric"]),
+    ("electrode passes 1 - T", "if (u[2] < sp[3]) {", "if (u[2] < 1.0 - sp[3]) {",
+     [PINS + "test_electrode_transparency"]),
+    ("quantum efficiency inverted", "if (u[2] < sp[2]) { fate = ORC_DETECTED; }",
+     "if (u[2] >= sp[2]) { fate = ORC_DETECTED; }", [PINS + "test_quantum_efficiency_and_tallies_consistent"]),
+    ("mirror reflection with the wrong sign", "dir[a] = dir[a] + 2.0 * cos_i * Nf[a];",
+     "dir[a] = dir[a] - 2.0 * cos_i * Nf[a];", [PINS + "test_mirror_sphere_normal_incidence_series"]),
+    ("volume source radius not square-rooted", "double r = R * sqrt(w[0]), a = TWO_PI * w[1];",
+     "double r = R * w[0], a = TWO_PI * w[1];", [PINS + "test_volume_source_uniform_isotropic"]),
+    ("source directions on a hemisphere", "draw4(seed, pid, SOURCE_STEP, 0, u);\n    double c = 2.0 * u[0] - 1.0",
+     "draw4(seed, pid, SOURCE_STEP, 0, u);\n    double c = u[0]", [PINS + "test_volume_source_uniform_isotropic"]),
+    ("refraction offset to the reflected side", "spawn_offset(pos, o_ray, th, Nf, refl ? 1.0 : -1.0);",
+     "spawn_offset(pos, o_ray, th, Nf, refl ? -1.0 : 1.0);", [PINS + "test_total_internal_reflection_on_shared_edges"]),
+    ("one-sided triangle test",
+     "if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return 0;",
+     "if (U < 0.0f || V < 0.0f || W < 0.0f) return 0;",
+     [PINS + "test_intersection_axis_aligned_square_closed_form", PINS + "test_watertight_closed_sphere"]),
+    ("BVH ties broken to the largest triangle id",
+     "uint32_t i = s->order[k];\n                float t;\n                if (i == skip) continue;\n"
+     "                if (wray_hit(&r, &s->v[9ull * i], bt, &t)) {\n"
+     "                    if (t < bt || (t == bt && (best == NO_HIT || i < best)))",
+     "uint32_t i = s->order[k];\n                float t;\n                if (i == skip) continue;\n"
+     "                if (wray_hit(&r, &s->v[9ull * i], bt, &t)) {\n"
+     "                    if (t < bt || (t == bt && (best == NO_HIT || i > best)))",
+     [PINS + "test_ties_go_to_the_smallest_index"]),
+    ("singlet and triplet time constants swapped", "double tau = w[0] < p[14] ? p[15] : p[16];",
+     "double tau = w[0] < p[14] ? p[16] : p[15];", [TIME + "test_nr_profile_mixture_cdf"]),
+    ("spectrum FWHM taken as two sigma", "double sigma = p[18] / (2.0 * sqrt(2.0 * log(2.0)));",
+     "double sigma = p[18] / 2.0;", [SPEC + "test_lxe_spectrum_is_the_gaussian_of_its_mean_and_fwhm"]),
+    ("dispersion with the wrong sign", "return mat[0] + mat[3] * (wl - REF_WAVELENGTH_NM);",
+     "return mat[0] - mat[3] * (wl - REF_WAVELENGTH_NM);", [SPEC + "test_dispersed_index_moves_the_reflection_series"]),
+    ("Rayleigh-length scaling inverted", "pow(wl / REF_WAVELENGTH_NM, mat[4])", "pow(REF_WAVELENGTH_NM / wl, mat[4])",
+     [SPEC + "test_rayleigh_length_scaling"]),
+    ("absorption-length score over L instead of L^2", "j[2 * i] = isinf(La) ? 0.0 : t[2 * i] / (La * La);",
+     "j[2 * i] = isinf(La) ? 0.0 : t[2 * i] / La;", [ADJ + "test_adjoint_exponential_survival"]),
+    ("Rayleigh-length score with the wrong sign", "t[2 * i] / (Lr * Lr) - t[2 * i + 1] / Lr",
+     "t[2 * i] / (Lr * Lr) + t[2 * i + 1] / Lr", [ADJ + "test_adjoint_rayleigh_length_zero_when_all_detected"]),
+    ("electrode score with the wrong sign", "g = a / sp[3] - b / (1.0 - sp[3]);", "g = a / sp[3] + b / (1.0 - sp[3]);",
+     [ADJ + "test_adjoint_electrode_transparency"]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, pins, tmp_path):
+    from oracle import build
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert src.count(old) == 1, f"mutation site of '{name}' not unique"
+    (tmp_path / "oracle.c").write_text(src.replace(old, new))
+    shutil.copy(os.path.join(ROOT, "oracle", "oracle.h"), tmp_path / "oracle.h")
+    lib = str(tmp_path / "liboracle_mutant.so")
+    build.compile_library(str(tmp_path / "oracle.c"), lib)
+    env = dict(os.environ, ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu",
+                        *pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"'{name}' survived {pins}:\n{r.stdout[-2000:]}"

@@ -32,6 +32,16 @@ def test_uniform_mapping_range():
     assert 0.0 < O.uniform(0x12345678) < 1.0
 
 
+def test_philox_known_answers():
+    """The published known-answer vectors of Philox4x32-10 (tests/golden),
+    which fix every round constant and the order of the words."""
+    from tests.golden.load import philox_kat
+    rows = philox_kat()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        assert [int(x) for x in O.philox(ctr, key)] == want
+
+
 def test_philox_counter_sensitivity_and_uniformity():
     key = np.array([7, 11], np.uint32)
     outs = np.array([O.philox([i, 0, 0, 0], key) for i in range(4096)], np.uint64)
@@ -259,6 +269,36 @@ def test_bvh_equals_brute_force_on_soup():
     assert (hb != 0xFFFFFFFF).sum() > n // 4
 
 
+def test_ties_go_to_the_smallest_index():
+    """Exact ties: a soup whose first 400 triangles are repeated under ids
+    1000..1399.  Every hit on a repeated triangle is a tie at the same t,
+    and the smaller index wins, in the BVH as in the brute-force search."""
+    from dataclasses import replace
+    base = g.random_soup(1000, seed=5)
+    extra = base.tris[:400]
+    det = replace(base, tris=np.concatenate([base.tris, extra]),
+                  mat_inner=np.concatenate([base.mat_inner, base.mat_inner[:400]]),
+                  mat_outer=np.concatenate([base.mat_outer, base.mat_outer[:400]]),
+                  surface=np.concatenate([base.surface, base.surface[:400]]),
+                  channel=np.concatenate([base.channel, base.channel[:400]]))
+    o = O.Oracle(det)
+    rng = np.random.default_rng(6)
+    n = 2000
+    tv = det.verts[det.tris[:400]].astype(np.float64)
+    k = rng.integers(0, 400, n)
+    w = rng.dirichlet([1, 1, 1], n)
+    tgt = np.einsum("nj,njk->nk", w, tv[k])
+    org = (tgt + rng.normal(0, 60, (n, 3))).astype(np.float32)
+    d = tgt - org
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    hb, tb = o.trace(org, d, None, None, brute=True)
+    hv, tv2 = o.trace(org, d, None, None, brute=False)
+    assert np.array_equal(hb, hv) and np.array_equal(tb, tv2)
+    hit = hb != 0xFFFFFFFF
+    assert np.sum(hit & (hb < 400)) > n // 2
+    assert not np.any(hit & (hb >= 1000))
+
+
 def test_watertight_closed_sphere():
     det = g.icosphere(50.0, subdiv=3)
     o = O.Oracle(det)
@@ -305,6 +345,31 @@ def test_worked_example_e1_reflection_series():
     assert res["fates"][O.ESCAPED] == 0 and res["fates"][O.GEOM_ERR] == 0
 
 
+def test_total_internal_reflection_on_shared_edges():
+    """Photons aimed exactly along the edges that the triangles of the liquid
+    surface share (its fan's diagonals x = +-y) at 45 deg, above the LXe/GXe
+    critical angle: every one is totally reflected back into the liquid and
+    reaches the bottom photocathode.  None comes back through the
+    neighbouring triangle of the edge, which a reflected photon left on the
+    wrong side of the surface would (Sec. 3, Appendix item 2 on shared
+    edges)."""
+    det = g.layered_box()
+    o = O.Oracle(det)
+    n = 4000
+    rng = np.random.default_rng(4)
+    a = rng.uniform(-300, 300, n).astype(np.float32)
+    sgn = np.where(np.arange(n) % 2 == 0, 1.0, -1.0).astype(np.float32)
+    pos = np.stack([a, sgn * a, np.full(n, -50.0, np.float32)], 1).astype(np.float32)
+    s = np.float32(math.sin(math.radians(45.0)) / math.sqrt(2.0))
+    d = np.stack([np.full(n, s), sgn * s, np.full(n, np.float32(math.cos(math.radians(45.0))))], 1)
+    d = d.astype(np.float32)
+    e = np.cross(d, rng.normal(size=(n, 3)))
+    pol = (e / np.linalg.norm(e, axis=1, keepdims=True)).astype(np.float32)
+    res = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=(pos, d, pol))
+    assert res["fates"][O.GEOM_ERR] == 0 and res["fates"][O.ESCAPED] == 0
+    assert res["lce"][0] == n and res["lce"][1] == 0
+
+
 def test_worked_example_e2_total_internal_reflection():
     """Sec. 3 second check: 75 deg on the LXe/quartz window reflects 100 %."""
     det = g.layered_box(with_gas=False)
@@ -349,6 +414,24 @@ def test_escape_from_absorbing_sphere(tau):
     res = o.propagate(n, seed=3)
     P = 3.0 / (8 * tau ** 3) * (2 * tau ** 2 - 1 + (1 + 2 * tau) * math.exp(-2 * tau))
     assert abs(res["lce"][0] / n - P) < 4 * binom_sigma(P, n) + 2e-3
+
+
+def test_competing_absorption_and_rayleigh():
+    """Absorption and Rayleigh scattering are independent exponential
+    processes (their own uniforms of the step): a photon crosses R unscattered
+    and unabsorbed with probability exp(-R/L_abs - R/L_ray), and its first
+    interaction is an absorption with probability L_ray / (L_abs + L_ray)."""
+    la, lr, R = 150.0, 100.0, 100.0
+    det = g.icosphere(R, subdiv=5, abs_len_mm=la, ray_len_mm=lr, n_medium=N_LXE)
+    o = O.Oracle(det)
+    n = 100_000
+    res = o.propagate(n, per_photon=True, seed=9)
+    direct = (res["steps"] == 1) & (res["fate"] == O.DETECTED)
+    p = math.exp(-R / la - R / lr)
+    assert abs(direct.mean() - p) < 4 * binom_sigma(p, n) + 2e-4
+    first_abs = (res["steps"] == 1) & (res["fate"] == O.BULK_ABS)
+    q = (1 - p) * lr / (la + lr)
+    assert abs(first_abs.mean() - q) < 4 * binom_sigma(q, n) + 2e-4
 
 
 def test_rayleigh_mean_free_path_and_time():
