@@ -87,6 +87,28 @@ MUTANTS = [
      "t[2 * i] / (Lr * Lr) + t[2 * i + 1] / Lr", [ADJ + "test_adjoint_rayleigh_length_zero_when_all_detected"]),
     ("electrode score with the wrong sign", "g = a / sp[3] - b / (1.0 - sp[3]);", "g = a / sp[3] + b / (1.0 - sp[3]);",
      [ADJ + "test_adjoint_electrode_transparency"]),
+    ("reflector specular decision inverted", "reflect_specular = u[3] < sp[1];", "reflect_specular = u[3] >= sp[1];",
+     [PINS + "test_specular_share_of_reflections[reflector]"]),
+    ("electrode wire specular decision inverted", "reflect_specular = w[3] < sp[5];",
+     "reflect_specular = w[3] >= sp[5];", [PINS + "test_specular_share_of_reflections[electrode]"]),
+    ("arrival-time bin off by one", "double b = floor(time / tbin);", "double b = floor(time / tbin) + 1.0;",
+     [PINS + "test_arrival_histogram_bins_the_photon_times"]),
+    ("emission start time t0 dropped", "*t0 = p[13];", "*t0 = 0.0;", [TIME + "test_no_profile_starts_at_t0"]),
+    ("light collection counts detected photons only",
+     "if (fate == ORC_DETECTED || fate == ORC_QE_FAIL) ty->lce[detail] += 1;",
+     "if (fate == ORC_DETECTED) ty->lce[detail] += 1;", [PINS + "test_quantum_efficiency_and_tallies_consistent"]),
+    ("adjoint: path to a surface not tallied", "if (ms >= 0) tl[2 * ms] += (double)th;", "",
+     [ADJ + "test_adjoint_exponential_survival"]),
+    ("adjoint: Rayleigh scatters not counted", "if (ms >= 0) tl[2 * ms + 1] += 1.0;", "",
+     [ADJ + "test_adjoint_rayleigh_length_zero_when_all_detected"]),
+    ("adjoint: reflections not counted",
+     "if (ss >= 0) tl[2 * na + 2 * ss] += 1.0;\n            reflect_specular = u[3] < sp[1];",
+     "reflect_specular = u[3] < sp[1];", [ADJ + "test_adjoint_mirror_reflectivity"]),
+    ("adjoint: electrode transmissions not counted",
+     "if (ss >= 0) tl[2 * na + 2 * ss] += 1.0;\n                medium = to;", "medium = to;",
+     [ADJ + "test_adjoint_electrode_transparency"]),
+    ("adjoint: wire reflections not counted", "if (ss >= 0) tl[2 * na + 2 * ss + 1] += 1.0;", "",
+     [ADJ + "test_adjoint_electrode_transparency"]),
 ]
 
 

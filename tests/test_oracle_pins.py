@@ -479,6 +479,48 @@ def test_reflector_absorption_geometric():
     assert abs(res["steps"].mean() - mean) < 5 * sd / math.sqrt(n)
 
 
+@pytest.mark.parametrize("kind", ["reflector", "electrode"])
+def test_specular_share_of_reflections(kind):
+    """Photons from the centre of a lossless reflecting sphere: a specular
+    first reflection sends the photon back through the centre (second leg
+    about 2R), a Lambertian one along a chord 2R cos(theta) with cos(theta) =
+    sqrt(u), longer than 2R (1 - d) with probability 1 - (1 - d)^2 only.  The
+    share of long second legs is the specular fraction f (+ that small
+    Lambertian share); both the reflector and the wire reflection of an
+    electrode follow it."""
+    f, R, dl = 0.3, 100.0, 3e-3
+    if kind == "reflector":
+        det = g.icosphere(R, subdiv=5, surface_type=g.REFLECTOR)
+        det.surfaces[0] = g.Surface("mirror", g.REFLECTOR, reflectivity=1.0, spec_frac=f)
+    else:
+        det = g.icosphere(R, subdiv=5, surface_type=g.ELECTRODE_T)
+        det.surfaces[0] = g.Surface("wires", g.ELECTRODE_T, transparency=0.0, wire_reflectivity=1.0,
+                                    wire_spec_frac=f)
+    n = 100_000
+    res = O.Oracle(det).propagate(n, per_photon=True, seed=12, max_steps=2)
+    assert np.all(res["fate"] == O.TRUNCATED)
+    leg2 = res["time"].astype(np.float64) * 299.792458 / det.materials[0].n - R
+    long = np.mean(leg2 > 2 * R * (1 - dl))
+    p = f + (1 - f) * (1 - (1 - dl) ** 2)
+    assert abs(long - p) < 4 * binom_sigma(p, n) + 2e-3, (long, p)
+
+
+def test_arrival_histogram_bins_the_photon_times():
+    """The per-channel arrival histogram is the binning of the detected
+    photons' own times: bin floor(t / width), the last bin for t beyond
+    the range."""
+    det = g.small_tpc()
+    n, width, bins = 40_000, 0.25, 8
+    res = O.Oracle(det).propagate(n, per_photon=True, seed=13, tbin_ns=width, n_tbins=bins)
+    det_ph = res["fate"] == O.DETECTED
+    ch, t = res["detail"][det_ph], res["time"][det_ph].astype(np.float64)
+    b = np.minimum(np.floor(t / width), bins).astype(np.int64)
+    want = np.zeros((det.n_pmts, bins + 1), np.int64)
+    np.add.at(want, (ch, b), 1)
+    assert np.array_equal(res["hist"].astype(np.int64), want)
+    assert want[:, bins].sum() > 0 and want[:, :bins].sum() > 0
+
+
 def test_electrode_transparency():
     T, Rw = 0.9, 0.3
     det = g.electrode_box(T, Rw)
