@@ -10,7 +10,10 @@
 //                      global atomic work queue: no lane idles while photons
 //                      remain.  Fate tallies live in shared memory per CTA;
 //                      per-channel counts and the time histogram use global
-//                      atomics.
+//                      atomics.  Template builds <kStats, kAdjoint, kSpectral>
+//                      add traversal counters, the adjoint tallies, and a
+//                      wavelength carried by each photon (dispersion); the
+//                      default build <0,0,0> has none of them.
 //
 // Bit-exactness of the closest hit: the triangle test below performs the same
 // IEEE float operations, in the same order, as a plain C implementation of
