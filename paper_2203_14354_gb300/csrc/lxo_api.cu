@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lxo_internal.h"
 
 struct lxo_ctx {
@@ -48,6 +50,16 @@ struct lxo_ctx {
 };
 
 namespace {
+
+// NVTX range over the host side of one API call (the launch enqueue for the
+// asynchronous ones): profilers attribute each kernel to the call that
+// launched it.  Free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct DeviceGuard {
     int prev = -1;
@@ -298,6 +310,7 @@ lxo_status lxo_load_mesh(lxo_ctx* c, const float* verts, uint32_t nv, const uint
                          const uint8_t* mat_inner, const uint8_t* mat_outer, const uint16_t* surface,
                          const int32_t* channel)
 {
+    NvtxRange nvtx("lxo_load_mesh");
     if (!c) return LXO_ERR_ARG;
     if (!verts || !tris || !mat_inner || !mat_outer || !surface || !channel)
         return fail(c, LXO_ERR_ARG, "load_mesh: NULL array");
@@ -381,6 +394,7 @@ lxo_status lxo_set_pmts(lxo_ctx* c, const lxo_pmt* p, uint32_t n)
 
 lxo_status lxo_build_bvh(lxo_ctx* c, const lxo_bvh_params* bp, lxo_bvh_info* info)
 {
+    NvtxRange nvtx("lxo_build_bvh");
     if (!c) return LXO_ERR_ARG;
     if (!c->have_mesh) return fail(c, LXO_ERR_STATE, "build_bvh: no mesh loaded");
     lxo_bvh_params q{};
@@ -465,6 +479,7 @@ lxo_status lxo_build_bvh(lxo_ctx* c, const lxo_bvh_params* bp, lxo_bvh_info* inf
 lxo_status lxo_trace_rays(lxo_ctx* c, const float* org, const float* dir, const uint32_t* skip, const float* tmax,
                           uint32_t n, uint32_t* hit, float* t, void* stream)
 {
+    NvtxRange nvtx("lxo_trace_rays");
     if (!c) return LXO_ERR_ARG;
     if (!c->have_bvh) return fail(c, LXO_ERR_STATE, "trace_rays: BVH not built");
     if (n == 0) return LXO_OK;
@@ -477,6 +492,7 @@ lxo_status lxo_trace_rays(lxo_ctx* c, const float* org, const float* dir, const 
 lxo_status lxo_sample_source(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, uint64_t seed,
                              float* pos, float* dir, float* pol, float* time, float* wavelength, void* stream)
 {
+    NvtxRange nvtx("lxo_sample_source");
     if (!c) return LXO_ERR_ARG;
     if (c->mats.empty()) return fail(c, LXO_ERR_STATE, "sample_source: no materials set");
     if (n == 0) return LXO_OK;
@@ -493,6 +509,7 @@ lxo_status lxo_sample_source(lxo_ctx* c, const lxo_source* src, uint64_t n, uint
 lxo_status lxo_propagate(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base, const lxo_run_params* rp,
                          const lxo_results* out, void* stream)
 {
+    NvtxRange nvtx("lxo_propagate");
     if (!c) return LXO_ERR_ARG;
     lxo_status s = validate(c);
     if (s) return s;
@@ -518,6 +535,7 @@ lxo_status lxo_propagate(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t
 lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t base,
                               const lxo_run_params* rp, const lxo_results* host_out, void* stream)
 {
+    NvtxRange nvtx("lxo_propagate_host");
     if (!c) return LXO_ERR_ARG;
     lxo_status s = validate(c);
     if (s) return s;
@@ -566,6 +584,7 @@ lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uin
 
 lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n)
 {
+    NvtxRange nvtx("lxo_upload_events");
     if (!c) return LXO_ERR_ARG;
     if (!ev || n == 0) return fail(c, LXO_ERR_ARG, "upload_events: no events");
     std::vector<lxo::EventDev> h(n);
@@ -608,6 +627,7 @@ lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n)
 
 lxo_status lxo_propagate_events(lxo_ctx* c, const lxo_run_params* rp, const lxo_results* out, void* stream)
 {
+    NvtxRange nvtx("lxo_propagate_events");
     if (!c) return LXO_ERR_ARG;
     lxo_status s = validate(c);
     if (s) return s;
@@ -684,6 +704,7 @@ lxo_status lxo_set_adjoint(lxo_ctx* c, const int32_t* mats, uint32_t n_mats, con
 lxo_status lxo_adjoint_jacobian(lxo_ctx* c, const double* sums, uint32_t n_rows, double* J, const double* g,
                                 double* grad, void* stream)
 {
+    NvtxRange nvtx("lxo_adjoint_jacobian");
     if (!c) return LXO_ERR_ARG;
     if (!sums || !J || (!g) != (!grad)) return fail(c, LXO_ERR_ARG, "adjoint_jacobian: NULL array");
     const int nm = (int)c->adj_mats.size(), ns = (int)c->adj_surfs.size();
