@@ -31,7 +31,6 @@ launch of the propagation kernel plus the Jacobian kernel of the library.
 """
 from __future__ import annotations
 
-import math
 import time
 
 import torch

@@ -8,8 +8,6 @@ import json
 import sys
 from contextlib import redirect_stdout
 
-import pytest
-
 import bench
 from paper_2203_14354_gb300 import geometry as g
 

@@ -8,9 +8,6 @@ import sys
 
 import numpy as np
 import pytest
-import torch
-
-from paper_2203_14354_gb300 import geometry as g
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
