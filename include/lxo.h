@@ -170,10 +170,13 @@ typedef struct {
 typedef struct {
     uint64_t seed;
     uint32_t max_steps;   /* interactions per photon before it is cut as TRUNCATED (0 = 10000) */
-    uint32_t n_tbins;     /* arrival-time bins per channel; bin n_tbins is the overflow */
+    uint32_t n_tbins;     /* arrival-time bins per channel, <= LXO_MAX_TBINS; bin n_tbins is the overflow */
     float tbin_ns;        /* bin width (> 0) */
     uint32_t flags;       /* LXO_FLAG_* */
 } lxo_run_params;
+
+/* largest n_tbins (LXO_ERR_ARG above it) */
+#define LXO_MAX_TBINS (1u << 24)
 
 /* run flags */
 #define LXO_FLAG_STATS 1u    /* count traversal work into lxo_results.stats (a separate kernel build) */

@@ -906,7 +906,7 @@ static void* worker(void* arg)
 int orc_propagate(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
                   uint32_t max_steps, double tbin_ns, uint32_t n_tbins, orc_results* out, int n_threads)
 {
-    if (!s || !src || !out || s->n_mat < 1 || s->n_chan < 1 || tbin_ns <= 0.0) return -1;
+    if (!s || !src || !out || s->n_mat < 1 || s->n_chan < 1 || tbin_ns <= 0.0 || n_tbins > (1u << 24)) return -1;
     int medium0 = (int)src->src[1];
     if (medium0 < 0 || medium0 >= s->n_mat) return -1;
     if (n_threads < 1) n_threads = 1;

@@ -92,6 +92,7 @@ typedef struct {
 
 int orc_propagate(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
                   uint32_t max_steps, double tbin_ns, uint32_t n_tbins, orc_results* out, int n_threads);
+/* returns -1 for bad arguments: no materials or channels, tbin_ns <= 0, n_tbins > 2^24 */
 
 /* Score-function adjoint: per photon, tally the path length and the Rayleigh
  * count in each tracked material and, for each tracked surface, the number

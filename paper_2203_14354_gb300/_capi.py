@@ -19,6 +19,7 @@ LXO_FLAG_STATS = 1
 LXO_FLAG_ADJOINT = 2
 LXO_STATIC_SCRATCH_BYTES = 8 << 20
 LXO_REF_WAVELENGTH_NM = 175.0
+LXO_MAX_TBINS = 1 << 24
 FATE_NAMES = ["detected", "qe_fail", "bulk_abs", "surf_abs", "escaped", "truncated", "geom_err"]
 
 

@@ -239,6 +239,8 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
         p->tbin = rp->tbin_ns;
         p->flags = rp->flags;
         if (!(rp->tbin_ns > 0.0f)) return fail(c, LXO_ERR_ARG, "tbin_ns must be > 0");
+        if (rp->n_tbins > LXO_MAX_TBINS)
+            return fail(c, LXO_ERR_ARG, "n_tbins %u above %u", rp->n_tbins, LXO_MAX_TBINS);
     }
     p->queue = c->d_queue;
     p->err = c->d_err;

@@ -75,3 +75,23 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[f"{c.__name__} size"]) == ctypes.sizeof(c), c.__name__
         for f in c._fields_:
             assert int(got[f"{c.__name__} {f[0]}"]) == getattr(c, f[0]).offset, (c.__name__, f[0])
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Every LXO_* constant the binding defines has the value of the macro or
+    enumerator of the same name in include/lxo.h."""
+    import subprocess
+    names = [k for k, v in vars(_capi).items() if k.startswith("LXO_") and isinstance(v, (int, float))]
+    assert {"LXO_MAX_TBINS", "LXO_FLAG_ADJOINT", "LXO_SURF_NONE", "LXO_ERR_CUDA"} <= set(names)
+    lines = ["#include <stdio.h>", '#include "lxo.h"', "int main(void) {"]
+    for n in names:
+        lines.append(f'printf("{n} %.17g\\n", (double)({n}));')
+    lines.append("return 0; }")
+    (tmp_path / "consts.c").write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(tmp_path / "consts.c"), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = dict(zip(out[0::2], map(float, out[1::2])))
+    for n in names:
+        assert got[n] == float(getattr(_capi, n)), n

@@ -9,6 +9,7 @@ import torch
 
 import oracle as O
 from paper_2203_14354_gb300 import geometry as g
+from paper_2203_14354_gb300 import _capi as A
 from paper_2203_14354_gb300._capi import LxoError
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +52,10 @@ def test_invalid_arguments_are_rejected(small):
         trk.upload_events([(g.Source(g.SRC_POINT, g.LXE).with_profile((0.5, -1.0, 24.0)), 10)])
     with pytest.raises(LxoError):
         trk.propagate(100, tbin_ns=0.0)
+    # n_tbins + 1 must not wrap: bins are capped at LXO_MAX_TBINS
+    for nb in (A.LXO_MAX_TBINS + 1, 0xFFFFFFFF):
+        with pytest.raises(LxoError, match="n_tbins"):
+            trk.propagate(100, n_tbins=nb, out=trk.alloc_results(4))
     # nothing ran, nothing broke: the same run gives the same tallies
     again = trk.propagate(5000, seed=3)
     for k in ("lce", "det", "hist", "fates"):
