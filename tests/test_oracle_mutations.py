@@ -6,7 +6,13 @@ with the oracle's own flags, and the pins named beside the mistake are run
 against it in a subprocess (ORACLE_LIB selects the library). At least one
 of them must fail. The unmodified oracle passes every pin (the rest of the
 suite), so a surviving mutant would mark a part of the oracle that no pin
-fixes."""
+fixes.
+
+Two mistakes are left out because they change no result: both remove one of
+two safeguards. Not skipping the last triangle hit changes nothing, because
+the spawn offset already keeps a photon off that surface. Dropping the
+1e-3 mm margin of the oracle's box test changes nothing, because its
+double-precision slab test on exact float boxes never needed it."""
 import os
 import shutil
 import subprocess
@@ -109,6 +115,19 @@ MUTANTS = [
      [ADJ + "test_adjoint_electrode_transparency"]),
     ("adjoint: wire reflections not counted", "if (ss >= 0) tl[2 * na + 2 * ss + 1] += 1.0;", "",
      [ADJ + "test_adjoint_electrode_transparency"]),
+    ("Philox Weyl constant off by one", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE86u;",
+     [PINS + "test_philox_known_answers"]),
+    ("counter: photon id words swapped", "uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), step, draw};",
+     "uint32_t ctr[4] = {(uint32_t)(pid >> 32), (uint32_t)pid, step, draw};", [PINS + "test_draw_contract"]),
+    ("counter: step and draw swapped", "uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), step, draw};",
+     "uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), draw, step};", [PINS + "test_draw_contract"]),
+    ("key: seed words swapped", "uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};",
+     "uint32_t key[2] = {(uint32_t)(seed >> 32), (uint32_t)seed};", [PINS + "test_draw_contract"]),
+    ("no spawn offset after a surface", "double eps = ldexp(m, -18);", "double eps = 0.0 * m;",
+     [PINS + "test_total_internal_reflection_on_shared_edges"]),
+    ("no special case at normal incidence",
+     "if (norm3(s) < 1e-6) {\n        s[0] = eps[0]; s[1] = eps[1]; s[2] = eps[2];\n    } else {\n        normalize3(s);\n    }",
+     "normalize3(s);", [PINS + "test_normal_incidence_keeps_photon", PINS + "test_worked_example_e1_reflection_series"]),
 ]
 
 

@@ -42,6 +42,44 @@ def test_philox_known_answers():
         assert [int(x) for x in O.philox(ctr, key)] == want
 
 
+def test_draw_contract():
+    """The oracle draws what the documented contract says, re-derived here
+    from the pinned Philox and uniform mapping: key = (seed low, seed high),
+    counter = (photon id low, high, step, draw); the source step is
+    0xFFFFFFFF, its draw 0 gives cos(theta) = 2 u0 - 1 of an isotropic
+    direction; the emission draw (draw 0xFFFFFFFF) picks the time-profile
+    component from u0, the delay from u1 and the wavelength from u2, u3
+    (Box-Muller); in step 0, draw 0's u0 sets the absorption distance
+    -L ln u0.  Ids and seeds have non-zero high words."""
+    seed = (3 << 32) | 11
+    pids = [(7 << 32) | 5, (1 << 40) | 123, 42]
+
+    def u(pid, step, draw):
+        ctr = [pid & 0xFFFFFFFF, pid >> 32, step, draw]
+        return [O.uniform(int(x)) for x in O.philox(ctr, [seed & 0xFFFFFFFF, seed >> 32])]
+
+    det = g.icosphere(1000.0, subdiv=3, abs_len_mm=50.0, n_medium=N_LXE)
+    o = O.Oracle(det)
+    f, ts, tt = g.NR_PROFILE
+    src = g.Source(g.SRC_POINT, 0).with_profile(g.NR_PROFILE).with_spectrum(g.LXE_SPECTRUM)
+    sigma = g.LXE_SPECTRUM[1] / (2 * math.sqrt(2 * math.log(2)))
+    for pid in pids:
+        pos, d, pol, med, t, wl = o.sample_source(1, base=pid, seed=seed, src=src, time=True, wavelength=True)
+        a = u(pid, 0xFFFFFFFF, 0)
+        assert d[0, 2] == pytest.approx(2 * a[0] - 1, abs=1e-12)
+        assert math.atan2(d[0, 1], d[0, 0]) % (2 * math.pi) == pytest.approx(2 * math.pi * a[1], abs=1e-9)
+        e = u(pid, 0xFFFFFFFF, 0xFFFFFFFF)
+        tau = ts if e[0] < f else tt
+        assert t[0] == pytest.approx(-tau * math.log(e[1]), rel=1e-12)
+        z = math.sqrt(-2 * math.log(e[2])) * math.cos(2 * math.pi * e[3])
+        assert wl[0] == pytest.approx(g.LXE_SPECTRUM[0] + sigma * z, rel=1e-12)
+        # step 0: absorbed at -L ln u0 (the sphere is 20 absorption lengths away)
+        res = o.propagate(1, base=pid, seed=seed, src=g.Source(g.SRC_POINT, 0), per_photon=True)
+        assert res["fate"][0] == O.BULK_ABS and res["steps"][0] == 1
+        dist = -50.0 * math.log(u(pid, 0, 0)[0])
+        assert res["time"][0] == pytest.approx(dist * N_LXE / 299.792458, rel=1e-6)
+
+
 def test_philox_counter_sensitivity_and_uniformity():
     key = np.array([7, 11], np.uint32)
     outs = np.array([O.philox([i, 0, 0, 0], key) for i in range(4096)], np.uint64)
