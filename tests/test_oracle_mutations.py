@@ -131,16 +131,39 @@ MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_planted_mistake(name, old, new, pins, tmp_path):
+def _run_mutant(k, old, new, pins, tmp):
+    """Build mutant k and run its pins against it; returns (exit code, output)."""
     from oracle import build
     src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
-    assert src.count(old) == 1, f"mutation site of '{name}' not unique"
-    (tmp_path / "oracle.c").write_text(src.replace(old, new))
-    shutil.copy(os.path.join(ROOT, "oracle", "oracle.h"), tmp_path / "oracle.h")
-    lib = str(tmp_path / "liboracle_mutant.so")
-    build.compile_library(str(tmp_path / "oracle.c"), lib)
+    if src.count(old) != 1:
+        return -1, "mutation site not unique"
+    d = os.path.join(tmp, f"m{k}")
+    os.makedirs(d)
+    with open(os.path.join(d, "oracle.c"), "w") as f:
+        f.write(src.replace(old, new))
+    shutil.copy(os.path.join(ROOT, "oracle", "oracle.h"), os.path.join(d, "oracle.h"))
+    lib = os.path.join(d, "liboracle_mutant.so")
+    build.compile_library(os.path.join(d, "oracle.c"), lib)
     env = dict(os.environ, ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu",
                         *pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode == 1, f"'{name}' survived {pins}:\n{r.stdout[-2000:]}"
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """All mutants built and run concurrently (each in its own process)."""
+    import concurrent.futures as cf
+    tmp = str(tmp_path_factory.mktemp("mutants"))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        futs = [ex.submit(_run_mutant, k, old, new, pins, tmp) for k, (_, old, new, pins) in enumerate(MUTANTS)]
+        return [f.result() for f in futs]
+
+
+@pytest.mark.parametrize("k", range(len(MUTANTS)), ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(k, outcomes):
+    name, _, _, pins = MUTANTS[k]
+    code, out = outcomes[k]
+    assert code != -1, f"mutation site of '{name}' not unique"
+    assert code == 1, f"'{name}' survived {pins}:\n{out}"
