@@ -1,9 +1,9 @@
 /*
  * lxo.h -- C ABI of the GB300 optical-photon tracker for liquid-xenon TPCs.
  *
- * The library propagates 175 nm scintillation photons, one photon per GPU
- * lane, through a triangle-mesh detector to their fate, PMT channel and
- * arrival time: exponential bulk absorption and Rayleigh scattering, polarised
+ * The library propagates scintillation photons (175 nm, or a Gaussian
+ * emission spectrum), one photon per GPU lane, through a triangle-mesh
+ * detector to their fate, PMT channel and arrival time: exponential bulk absorption and Rayleigh scattering, polarised
  * Fresnel reflection / refraction with total internal reflection at
  * dielectric boundaries, reflectivity-parameterised surfaces (PTFE, stainless
  * steel), effective-transparency electrodes and photocathodes with a quantum
@@ -19,8 +19,9 @@
  *    completes.  Geometry, BVH and scratch memory are owned by the context.
  *  - Calls that take `stream` (a cudaStream_t; NULL = the legacy default
  *    stream) are asynchronous.  Faults detected inside a kernel (traversal
- *    stack overflow, channel out of range) set a device error word that
- *    lxo_sync() reads back and reports as LXO_ERR_DEVICE.
+ *    stack overflow, channel out of range, and in the bounds-checked build an
+ *    index outside its array) set a device error word that lxo_sync() reads
+ *    back and reports as LXO_ERR_DEVICE.
  *  - Result tallies ACCUMULATE: the caller zeroes them.  Photon p's random
  *    stream depends only on (seed, p), so splitting a run into several calls
  *    with disjoint photon_id_base ranges adds up to the same tallies.
