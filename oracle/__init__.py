@@ -37,7 +37,7 @@ class _Source(C.Structure):
 class _Results(C.Structure):
     _fields_ = [("lce", C.c_void_p), ("det", C.c_void_p), ("hist", C.c_void_p), ("fates", C.c_void_p),
                 ("ph_fate", C.c_void_p), ("ph_detail", C.c_void_p), ("ph_steps", C.c_void_p),
-                ("ph_time", C.c_void_p), ("adjoint", C.c_void_p)]
+                ("ph_time", C.c_void_p), ("adjoint", C.c_void_p), ("ph_state", C.c_void_p)]
 
 
 def lib():
@@ -70,6 +70,7 @@ def lib():
         L.orc_dielectric.restype = C.c_int
         L.orc_dielectric.argtypes = [f64p, f64p, f64p, C.c_double, C.c_double, C.c_double, f64p, f64p,
                                      C.POINTER(C.c_double)]
+        L.orc_mirror.argtypes = [f64p, f64p, f64p, f64p, f64p]
         L.orc_rayleigh.argtypes = [f64p, f64p, C.c_uint64, C.c_uint32, C.c_uint64, f64p, f64p]
         L.orc_lambert.argtypes = [f64p, C.c_uint64, C.c_uint32, C.c_uint64, f64p, f64p]
         _lib = L
@@ -182,7 +183,8 @@ class Oracle:
                    fates=np.zeros(N_FIXED + self.n_mat + self.n_surf, np.uint64))
         if per_photon:
             out.update(fate=np.zeros(n, np.uint32), detail=np.zeros(n, np.int32),
-                       steps=np.zeros(n, np.uint32), time=np.zeros(n, np.float32))
+                       steps=np.zeros(n, np.uint32), time=np.zeros(n, np.float32),
+                       state=np.zeros((n, 9), np.float32))
         if adjoint:
             out["adjoint"] = np.zeros((P, self.n_tallies), np.float64)
         r = _Results()
@@ -190,6 +192,7 @@ class Oracle:
         if per_photon:
             r.ph_fate, r.ph_detail = _ptr(out["fate"]), _ptr(out["detail"])
             r.ph_steps, r.ph_time = _ptr(out["steps"]), _ptr(out["time"])
+            r.ph_state = _ptr(out["state"])
         if adjoint:
             r.adjoint = _ptr(out["adjoint"])
         if threads is None:
@@ -224,6 +227,12 @@ def dielectric(k, eps, N, n1, n2, u):
     refl = lib().orc_dielectric(np.asarray(k, float), np.asarray(eps, float), np.asarray(N, float), n1, n2, u,
                                 ko, eo, C.byref(pr))
     return bool(refl), ko, eo, pr.value
+
+
+def mirror(k, eps, N):
+    ko, eo = np.zeros(3), np.zeros(3)
+    lib().orc_mirror(np.asarray(k, float), np.asarray(eps, float), np.asarray(N, float), ko, eo)
+    return ko, eo
 
 
 def rayleigh(k, eps, pid, step=0, seed=0):

@@ -195,27 +195,27 @@ static void tri_bounds(const float* v, float lo[3], float hi[3])
     }
 }
 
-static int g_axis;
-static int cref_cmp(const void* a, const void* b)
+/* order of two references by (centroid[axis], id); the axis is an argument
+ * so that scenes can be built from several threads at once */
+static int cref_cmp(const cref* a, const cref* b, int axis)
 {
-    float x = ((const cref*)a)->c[g_axis], y = ((const cref*)b)->c[g_axis];
+    float x = a->c[axis], y = b->c[axis];
     if (x < y) return -1;
     if (x > y) return 1;
-    uint32_t i = ((const cref*)a)->id, j = ((const cref*)b)->id;
-    return (i < j) ? -1 : (i > j);
+    return (a->id < b->id) ? -1 : (a->id > b->id);
 }
 
-/* quickselect by (centroid[axis], id) so the split is deterministic */
+/* quickselect by (centroid[axis], id) so the split is deterministic; the
+ * last few elements are put in order by insertion */
 static void select_kth(cref* a, uint32_t n, uint32_t k, int axis)
 {
-    g_axis = axis;
     uint32_t lo = 0, hi = n - 1;
     while (hi > lo + 16) {
         cref piv = a[lo + (hi - lo) / 2];
         uint32_t i = lo, j = hi;
         while (i <= j) {
-            while (cref_cmp(&a[i], &piv) < 0) ++i;
-            while (cref_cmp(&a[j], &piv) > 0) --j;
+            while (cref_cmp(&a[i], &piv, axis) < 0) ++i;
+            while (cref_cmp(&a[j], &piv, axis) > 0) --j;
             if (i <= j) {
                 cref t = a[i]; a[i] = a[j]; a[j] = t;
                 ++i;
@@ -227,7 +227,15 @@ static void select_kth(cref* a, uint32_t n, uint32_t k, int axis)
         else if (k >= i) lo = i;
         else return;
     }
-    qsort(a + lo, hi - lo + 1, sizeof(cref), cref_cmp);
+    for (uint32_t i = lo + 1; i <= hi; ++i) {
+        cref t = a[i];
+        uint32_t j = i;
+        while (j > lo && cref_cmp(&t, &a[j - 1], axis) < 0) {
+            a[j] = a[j - 1];
+            --j;
+        }
+        a[j] = t;
+    }
 }
 
 static uint32_t build_rec(orc_scene* s, cref* refs, uint32_t first, uint32_t count)
@@ -534,6 +542,26 @@ int orc_dielectric(const double k[3], const double eps[3], const double N[3], do
     for (int a = 0; a < 3; ++a) eps_out[a] = cs * f[2] * s[a] + cp * f[3] * pt_v[a];
     normalize3(eps_out);
     return 0;
+}
+
+/* Specular reflection off a reflector (Sec. 2.2: the specular share of a
+ * reflector's reflections): the direction mirrors about the surface,
+ * k' = k + 2 cos(i) N; the polarisation mirrors like a field reflected by a
+ * perfect conductor, whose tangential part changes sign and whose normal
+ * part is kept, eps' = -eps + 2 (eps.N) N, then made exactly transverse to
+ * k' and unit.  N is the unit normal on the incident side. */
+void orc_mirror(const double k[3], const double eps[3], const double N[3], double k_out[3], double eps_out[3])
+{
+    double cos_i = -dot3(k, N);
+    double pe = dot3(eps, N);
+    for (int a = 0; a < 3; ++a) {
+        k_out[a] = k[a] + 2.0 * cos_i * N[a];
+        eps_out[a] = -eps[a] + 2.0 * pe * N[a];
+    }
+    normalize3(k_out);
+    double c = dot3(eps_out, k_out);
+    for (int a = 0; a < 3; ++a) eps_out[a] -= c * k_out[a];
+    normalize3(eps_out);
 }
 
 /* Rayleigh scattering of a linearly polarised photon (dipole law, Appendix
@@ -845,16 +873,10 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
             fate = ORC_GEOM_ERR; detail = (int32_t)tri; break;
         }
         if (reflect_specular) {
-            double cos_i = -dot3(dir, Nf);
-            double pe = dot3(pol, Nf);
-            for (int a = 0; a < 3; ++a) {
-                dir[a] = dir[a] + 2.0 * cos_i * Nf[a];
-                pol[a] = -pol[a] + 2.0 * pe * Nf[a];
-            }
-            normalize3(dir);
-            double c = dot3(pol, dir);
-            for (int a = 0; a < 3; ++a) pol[a] -= c * dir[a];
-            normalize3(pol);
+            double k2[3], e2[3];
+            orc_mirror(dir, pol, Nf, k2, e2);
+            memcpy(dir, k2, sizeof k2);
+            memcpy(pol, e2, sizeof e2);
         } else {
             double k2[3], e2[3];
             orc_lambert(Nf, pid, step, seed, k2, e2);
@@ -883,6 +905,14 @@ static void run_photon(const orc_scene* s, const orc_source* src, uint64_t pid, 
     if (out->ph_detail) out->ph_detail[idx] = detail;
     if (out->ph_steps) out->ph_steps[idx] = steps;
     if (out->ph_time) out->ph_time[idx] = (float)time;
+    if (out->ph_state) {
+        float* o = out->ph_state + 9 * idx;
+        for (int a = 0; a < 3; ++a) {
+            o[a] = (float)pos[a];
+            o[3 + a] = (float)dir[a];
+            o[6 + a] = (float)pol[a];
+        }
+    }
 }
 
 typedef struct {

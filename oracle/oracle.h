@@ -88,6 +88,7 @@ typedef struct {
     float* ph_time;       /* optional [n]: time at the end (ns) */
     double* adjoint;      /* optional [P*K]: per-channel sums of the detected photons' tallies
                              (K = 2*n_mat + 2*n_surf of orc_set_adjoint) */
+    float* ph_state;      /* optional [n*9]: position, direction, polarisation at the end */
 } orc_results;
 
 int orc_propagate(const orc_scene* s, const orc_source* src, uint64_t n, uint64_t base, uint64_t seed,
@@ -116,6 +117,9 @@ void orc_fresnel(double n1, double n2, double cos_i, double out[6]);
  * out: k'[3], eps'[3]; returns 1 if reflected, 0 if refracted. */
 int orc_dielectric(const double k[3], const double eps[3], const double N[3], double n1, double n2,
                    double u, double k_out[3], double eps_out[3], double* p_reflect);
+/* specular reflection off a reflector: k' = k + 2 cos(i) N; eps' = -eps + 2 (eps.N) N made transverse
+ * to k' and unit (N unit, on the incident side) */
+void orc_mirror(const double k[3], const double eps[3], const double N[3], double k_out[3], double eps_out[3]);
 /* samplers driven by the photon's Philox stream (photon id, step) */
 void orc_rayleigh(const double k[3], const double eps[3], uint64_t pid, uint32_t step, uint64_t seed,
                   double k_out[3], double eps_out[3]);

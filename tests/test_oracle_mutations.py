@@ -59,8 +59,36 @@ MUTANTS = [
      [PINS + "test_electrode_transparency"]),
     ("quantum efficiency inverted", "if (u[2] < sp[2]) { fate = ORC_DETECTED; }",
      "if (u[2] >= sp[2]) { fate = ORC_DETECTED; }", [PINS + "test_quantum_efficiency_and_tallies_consistent"]),
-    ("mirror reflection with the wrong sign", "dir[a] = dir[a] + 2.0 * cos_i * Nf[a];",
-     "dir[a] = dir[a] - 2.0 * cos_i * Nf[a];", [PINS + "test_mirror_sphere_normal_incidence_series"]),
+    ("mirror reflection with the wrong sign",
+     "k_out[a] = k[a] + 2.0 * cos_i * N[a];\n        eps_out[a] = -eps[a] + 2.0 * pe * N[a];",
+     "k_out[a] = k[a] - 2.0 * cos_i * N[a];\n        eps_out[a] = -eps[a] + 2.0 * pe * N[a];",
+     [PINS + "test_mirror_sphere_normal_incidence_series"]),
+    ("mirror polarisation not reflected", "eps_out[a] = -eps[a] + 2.0 * pe * N[a];", "eps_out[a] = eps[a];",
+     [PINS + "test_mirror_polarisation_is_the_perfect_conductor_field", PINS + "test_mirror_then_brewster_surface"]),
+    ("mirror polarisation: normal part dropped", "eps_out[a] = -eps[a] + 2.0 * pe * N[a];",
+     "eps_out[a] = -eps[a] + pe * N[a];", [PINS + "test_mirror_polarisation_is_the_perfect_conductor_field"]),
+    ("transmitted polarisation with t_s and t_p swapped",
+     "eps_out[a] = cs * f[2] * s[a] + cp * f[3] * pt_v[a];", "eps_out[a] = cs * f[3] * s[a] + cp * f[2] * pt_v[a];",
+     [PINS + "test_outgoing_polarisation_satisfies_maxwell_boundary_conditions",
+      PINS + "test_two_interfaces_carry_the_refracted_polarisation"]),
+    ("transmitted p basis from the incident direction", "cross3(s, k_out, pt_v);", "cross3(s, k, pt_v);",
+     [PINS + "test_outgoing_polarisation_satisfies_maxwell_boundary_conditions"]),
+    ("reflected polarisation with r_s for both components",
+     "double as = tir ? cs : cs * f[0], ap = tir ? cp : cp * f[1];",
+     "double as = tir ? cs : cs * f[0], ap = tir ? cp : cp * f[0];",
+     [PINS + "test_outgoing_polarisation_satisfies_maxwell_boundary_conditions"]),
+    ("reflected p component with the wrong sign",
+     "double as = tir ? cs : cs * f[0], ap = tir ? cp : cp * f[1];",
+     "double as = tir ? cs : cs * f[0], ap = tir ? cp : -cp * f[1];",
+     [PINS + "test_outgoing_polarisation_satisfies_maxwell_boundary_conditions"]),
+    ("total internal reflection rotates the polarisation",
+     "double as = tir ? cs : cs * f[0], ap = tir ? cp : cp * f[1];",
+     "double as = tir ? cp : cs * f[0], ap = tir ? cs : cp * f[1];",
+     [PINS + "test_total_internal_reflection_keeps_the_polarisation_magnitudes"]),
+    ("total internal reflection flips the p component",
+     "double as = tir ? cs : cs * f[0], ap = tir ? cp : cp * f[1];",
+     "double as = tir ? cs : cs * f[0], ap = tir ? -cp : cp * f[1];",
+     [PINS + "test_total_internal_reflection_keeps_the_polarisation_magnitudes"]),
     ("volume source radius not square-rooted", "double r = R * sqrt(w[0]), a = TWO_PI * w[1];",
      "double r = R * w[0], a = TWO_PI * w[1];", [PINS + "test_volume_source_uniform_isotropic"]),
     ("source directions on a hemisphere", "draw4(seed, pid, SOURCE_STEP, 0, u);\n    double c = 2.0 * u[0] - 1.0",

@@ -15,6 +15,7 @@ from scipy import stats
 
 import oracle as O
 from paper_2203_14354_gb300 import geometry as g
+from tests import closed_forms as CF
 from tests.golden.load import paper_values
 
 PV = paper_values()
@@ -210,6 +211,209 @@ def test_normal_incidence_keeps_photon():
     assert pr == pytest.approx(((N_LXE - N_GXE) / (N_LXE + N_GXE)) ** 2, abs=1e-12)
     refl, ko, eo, pr = O.dielectric(k, eps, N, N_LXE, N_GXE, 1 - 1e-9)
     assert not refl and np.allclose(ko, k) and abs(abs(eo[0]) - 1) < 1e-12
+
+
+# ------------------------------------------------ outgoing polarisation -----
+# The outgoing polarisation of a dielectric step is pinned by Maxwell's
+# boundary conditions (Born & Wolf, Sec. 1.5.1), from which the Fresnel
+# formulae themselves follow: across the interface the tangential components
+# of E and of H = n k x E (non-magnetic media, units with c = mu = 1) are
+# continuous.  The incident wave (k, eps) with unit amplitude, the reflected
+# wave (k_r, e_r) and the transmitted wave (k_t, e_t) must therefore admit
+# amplitudes a_r, a_t that satisfy four equations at once.  The oracle
+# returns only normalised directions, so the test solves for a_r and a_t by
+# least squares and requires a zero residual; a polarisation rotated within
+# its plane (t_s and t_p swapped, r_s used for both components, a flipped p
+# component) leaves a residual of order one.
+def _tangential(v, N):
+    return v - (v @ N) * N
+
+
+def _maxwell_residual(k, eps, N, n1, n2, kr, er, kt, et):
+    A = np.zeros((6, 2))
+    b = np.zeros(6)
+    A[:3, 0], A[:3, 1] = _tangential(er, N), -_tangential(et, N)
+    b[:3] = -_tangential(eps, N)
+    A[3:, 0] = n1 * _tangential(np.cross(kr, er), N)
+    A[3:, 1] = -n2 * _tangential(np.cross(kt, et), N)
+    b[3:] = -n1 * _tangential(np.cross(k, eps), N)
+    amp, *_ = np.linalg.lstsq(A, b, rcond=None)
+    return float(np.linalg.norm(A @ amp - b)), amp
+
+
+def _both_branches(k, eps, N, n1, n2):
+    r1, kr, er, pr = O.dielectric(k, eps, N, n1, n2, 0.0)
+    r2, kt, et, _ = O.dielectric(k, eps, N, n1, n2, 1.0 - 1e-15)
+    assert r1 and not r2
+    return kr, er, kt, et, pr
+
+
+@pytest.mark.parametrize("n1,n2", [(N_LXE, N_GXE), (N_GXE, N_Q), (N_LXE, N_Q), (N_Q, N_GXE), (N_GXE, N_LXE)])
+def test_outgoing_polarisation_satisfies_maxwell_boundary_conditions(n1, n2):
+    """Reflected and transmitted polarisations of the coherent reading
+    (Sec. 2.2: Fresnel surfaces between LXe, GXe and quartz) at oblique
+    incidence, for linear polarisations between pure s and pure p and
+    interface normals in arbitrary orientation."""
+    rng = np.random.default_rng(17)
+    crit = math.degrees(math.asin(min(1.0, n2 / n1)))
+    for th in (5.0, 20.0, 30.61, 45.0, 60.0, 80.0):
+        if th >= crit - 0.5:
+            continue
+        for pa in (0.0, 0.4, 0.9, 1.3, math.pi / 2, 2.3):
+            R = np.linalg.qr(rng.normal(size=(3, 3)))[0]   # random rotation of the whole set-up
+            k, N, s, eps = (R @ v for v in _basis_case(th, pa))
+            kr, er, kt, et, pr = _both_branches(k, eps, N, n1, n2)
+            res, (ar, at) = _maxwell_residual(k, eps, N, n1, n2, kr, er, kt, et)
+            assert res < 1e-9, (th, pa, res)
+            # the amplitudes found carry the Fresnel energy balance:
+            # reflectance + transmitted flux = 1, reflectance = P(reflect)
+            ci, ct = -(k @ N), -(kt @ N)
+            assert ar * ar == pytest.approx(pr, abs=1e-9)
+            assert ar * ar + (n2 * ct) / (n1 * ci) * at * at == pytest.approx(1.0, abs=1e-9)
+
+
+def test_transmitted_polarisation_angle_from_boundary_conditions():
+    """The s / p mix of the refracted wave, tan(psi_t) = (t_p / t_s)
+    tan(psi_i), and of the reflected wave, tan(psi_r) = (r_p / r_s)
+    tan(psi_i) with p' = s x k', the amplitudes solved from the two boundary
+    conditions of each polarisation (not from their closed forms), at the
+    three interfaces of the detector (Sec. 2.2), away from Brewster's
+    angle."""
+    for n1, n2 in [(N_LXE, N_GXE), (N_GXE, N_Q), (N_LXE, N_Q)]:
+        for th in (15.0, 34.0, 50.0, 70.0):
+            c = CF.fresnel_bc(n1, n2, th)
+            if c is None:
+                continue
+            k, N, s, eps = _basis_case(th, 0.7)
+            kr, er, kt, et, _ = _both_branches(k, eps, N, n1, n2)
+            psi_t = math.atan2(et @ np.cross(s, kt), et @ s)
+            want = math.atan2(c["tp"] * math.sin(0.7), c["ts"] * math.cos(0.7))
+            assert math.tan(psi_t) == pytest.approx(math.tan(want), rel=1e-9)
+            want_r = c["rp"] * math.sin(0.7) / (c["rs"] * math.cos(0.7))
+            assert (er @ np.cross(s, kr)) / (er @ s) == pytest.approx(want_r, rel=1e-9)
+
+
+def test_total_internal_reflection_keeps_the_polarisation_magnitudes():
+    """Under total internal reflection both amplitudes have modulus one
+    (reading 1: the phases are dropped), so the s / p magnitudes of the
+    polarisation are kept; and the reflected polarisation is continuous
+    across the critical angle (its limit from below, where r_s, r_p -> 1),
+    which fixes the sign of the p component."""
+    for n1, n2 in [(N_LXE, N_GXE), (N_LXE, N_Q), (N_Q, N_GXE)]:
+        crit = math.degrees(math.asin(n2 / n1))
+        for th in (crit + 1.0, 0.5 * (crit + 90.0), 85.0):
+            for pa in (0.3, 1.0, 2.0):
+                k, N, s, eps = _basis_case(th, pa)
+                refl, kr, er, pr = O.dielectric(k, eps, N, n1, n2, 1.0 - 1e-15)
+                assert refl and pr == 1.0
+                assert abs(er @ s) == pytest.approx(abs(math.cos(pa)), abs=1e-12)
+                assert abs(er @ np.cross(s, kr)) == pytest.approx(abs(math.sin(pa)), abs=1e-12)
+        for pa in (0.3, 1.0, 2.0):
+            lo = _basis_case(crit - 1e-7, pa)
+            hi = _basis_case(crit + 1e-7, pa)
+            _, _, e_lo, _ = O.dielectric(lo[0], lo[3], lo[1], n1, n2, 0.0)
+            _, _, e_hi, _ = O.dielectric(hi[0], hi[3], hi[1], n1, n2, 0.0)
+            assert np.allclose(e_lo, e_hi, atol=2e-3), (n1, n2, pa, e_lo, e_hi)
+
+
+def test_mirror_polarisation_is_the_perfect_conductor_field():
+    """Specular reflection (Sec. 2.2, reflector surfaces): the law of
+    reflection, and a polarisation whose tangential part is the negative of
+    the incident one with the same modulus (the tangential E of a perfect
+    conductor vanishes: E_i,t + E_r,t = 0 at unit reflected amplitude), and
+    which is transverse to the reflected direction."""
+    rng = np.random.default_rng(23)
+    for _ in range(200):
+        N = rng.normal(size=3)
+        N /= np.linalg.norm(N)
+        k = rng.normal(size=3)
+        k -= (abs(k @ N) + 0.05) * N if k @ N > 0 else 0.0
+        k /= np.linalg.norm(k)
+        if k @ N > -0.02:
+            continue
+        eps = np.cross(k, rng.normal(size=3))
+        eps /= np.linalg.norm(eps)
+        kr, er = O.mirror(k, eps, N)
+        assert kr @ N == pytest.approx(-(k @ N), abs=1e-12)
+        assert np.allclose(_tangential(kr, N), _tangential(k, N), atol=1e-12)
+        assert abs(er @ kr) < 1e-12 and abs(np.linalg.norm(er) - 1) < 1e-12
+        assert np.allclose(_tangential(er, N), -_tangential(eps, N), atol=1e-9)
+
+
+def test_two_interfaces_carry_the_refracted_polarisation():
+    """An oblique beam, polarised half-way between s and p, crosses LXe ->
+    GXe -> quartz (the layered set-up of the Sec. 3 worked examples, beam at
+    34 deg, just below the LXe/GXe critical angle).  The s / p mix after the
+    first refraction sets the reflectance of the quartz window (there R_s =
+    0.36, R_p = 0.05), so the fraction reaching the top photocathode tests the
+    transmitted polarisation end to end.  Expected value: the exact series
+    of reflections between the window and the liquid surface, with the s
+    fraction carried through each step by amplitudes from the boundary
+    conditions."""
+    o = O.Oracle(g.layered_box())
+    n = 200_000
+    psi = math.radians(45.0)
+    res = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=CF.oblique_beam(n, 34.0, psi, -50.0))
+    assert res["fates"][O.ESCAPED] == 0 and res["fates"][O.GEOM_ERR] == 0
+    top = CF.top_fraction(N_LXE, N_GXE, N_Q, 34.0, math.cos(psi) ** 2)
+    frac = res["lce"][1] / n
+    assert abs(frac - top) < 4 * binom_sigma(top, n), (frac, top)
+    # with t_s and t_p exchanged the window's reflectance would move by > 0.05,
+    # more than 40 sigma of this beam
+    c1 = CF.fresnel_bc(N_LXE, N_GXE, 34.0)
+    c2 = CF.fresnel_bc(N_GXE, N_Q, CF.refraction_angle(N_LXE, N_GXE, 34.0))
+    f_ok = CF._after(0.5, c1["ts"], c1["tp"])
+    f_swap = CF._after(0.5, c1["tp"], c1["ts"])
+    assert abs(CF._reflectance(f_ok, c2) - CF._reflectance(f_swap, c2)) > 0.05
+
+
+@pytest.mark.parametrize("psi_deg", [45.0, 70.0])
+def test_mirror_then_brewster_surface(psi_deg):
+    """A beam in the LXe heads down at Brewster's angle of the liquid
+    surface (30.6 deg) onto a specular mirror of reflectivity 0.5, then up
+    to the surface, where only its s component can reflect back towards the
+    lossy mirror (R_p = 0, R_s = 0.23).  The top fraction therefore depends
+    on the s / p mix that the mirror leaves (Sec. 2.2 reflector surfaces;
+    Sec. 3 layered set-up).  Expected value: the exact series, the mirror
+    keeping the s fraction."""
+    th = math.degrees(math.atan(N_GXE / N_LXE))
+    o = O.Oracle(CF.mirror_floor_box(0.5))
+    n = 200_000
+    psi = math.radians(psi_deg)
+    res = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE),
+                      explicit=CF.oblique_beam(n, th, psi, -50.0, up=False))
+    assert res["fates"][O.ESCAPED] == 0 and res["fates"][O.GEOM_ERR] == 0
+    top = CF.top_fraction(N_LXE, N_GXE, N_Q, th, math.cos(psi) ** 2, first="mirror", mirror_floor=0.5)
+    frac = res["lce"][1] / n
+    assert abs(frac - top) < 4 * binom_sigma(top, n), (frac, top)
+
+
+def test_final_state_output_is_the_photon_state():
+    """The per-photon final state (the output through which the GPU's
+    outgoing waves are compared with the oracle's) holds the photon where
+    its last step left it: a beam sent up at 20 deg through the liquid
+    surface of the layered set-up stops after one step on the surface,
+    reflected by the law of reflection or refracted by Snell's law; after
+    two steps the reflected photons sit on the bottom photocathode."""
+    o = O.Oracle(g.layered_box())
+    n = 2000
+    beam = CF.oblique_beam(n, 20.0, 0.6, -50.0)
+    r1 = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=beam, max_steps=1, per_photon=True)
+    assert np.all(r1["fate"] == O.TRUNCATED) and np.all(r1["steps"] == 1)
+    st = r1["state"].astype(np.float64)
+    assert np.all(np.abs(st[:, 2]) < 1e-3)
+    assert np.allclose(st[:, :2] - beam[0][:, :2], 50.0 * math.tan(math.radians(20.0)) * np.array([1, 0]), atol=1e-3)
+    k = beam[1][0].astype(np.float64)
+    refl = st[:, 5] < 0
+    assert 0 < refl.sum() < n
+    assert np.allclose(st[refl, 3:6], k * [1, 1, -1], atol=1e-6)
+    assert np.allclose(st[~refl, 3], N_LXE / N_GXE * k[0], atol=1e-6)
+    assert np.allclose(np.linalg.norm(st[:, 6:9], axis=1), 1, atol=1e-6)
+    assert np.all(np.abs((st[:, 3:6] * st[:, 6:9]).sum(1)) < 1e-6)
+    r2 = o.propagate(n, src=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=beam, max_steps=2, per_photon=True)
+    down = r2["detail"] == 0
+    assert np.array_equal(down & (r2["fate"] == O.DETECTED), refl)
+    assert np.allclose(r2["state"][down, 2], -100.0, atol=1e-3)
 
 
 # ------------------------------------------------------------- Rayleigh -----
