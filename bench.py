@@ -15,8 +15,13 @@ collective on the data path); the timing is the max over ranks.
 
 --impl reference times the CPU oracle (the plain scalar C tracker) on the host
 cores on a bounded sample of the same workload.
+
+Output: one JSON line {"details": ...} with every per-ring, per-PMT and
+per-shape table, then the bench line itself, kept short enough to be read
+whole (the forward+adjoint ratio and the finite-difference summary last).
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -38,13 +43,20 @@ N_SM, LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) per photon of the propagation kernel: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of one timed launch on 2e6
 # photons of this workload (4.622 GB + 0.162 GB), divided by 2e6; scales with
-# the photon count.  None while the kernel differs from the one captured.
+# the photon count.
 DRAM_BYTES_PER_PHOTON = 2392
 # warp instructions issued per photon step by the same capture
 # (smsp__inst_executed.sum 1.2662e10 over 5.152e7 steps); the issue-slot peak
 # is 152 SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
 WARP_INST_PER_STEP = 246.0
 SCHEDULERS_PER_SM = 4
+# The kernel build those two numbers were captured from: its ptxas
+# signature and the SHA-256 of its sources.  When the built kernel differs,
+# the line says roofline.stale = true and drops traffic (the counters must
+# be taken again).
+TIMED_KERNEL = "_ZN3lxo11k_propagateILb0ELb0ELb0ELi256EEEvNS_10PropParamsE"   # k_propagate<0,0,0,256>
+KERNEL_SOURCES = ("paper_2203_14354_gb300/csrc/lxo_kernels.cu", "paper_2203_14354_gb300/csrc/lxo_internal.h")
+CAPTURED_KERNEL = {"registers": 48, "spill_stores": 264, "spill_loads": 292, "sources_sha256": None}
 
 
 def parse():
@@ -119,6 +131,33 @@ class ClockSampler:
         reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def kernel_signature():
+    """ptxas registers and spill bytes of the timed kernel in the library's
+    build log, and the SHA-256 of the kernel's sources."""
+    from paper_2203_14354_gb300 import build
+    sig = {"registers": None, "spill_stores": None, "spill_loads": None}
+    try:
+        lines = open(os.path.join(build.OUT_DIR, "ptxas.log")).read().splitlines()
+    except OSError:
+        lines = []
+    for i, ln in enumerate(lines):
+        if f"Compiling entry function '{TIMED_KERNEL}'" in ln:
+            for nxt in lines[i + 1:i + 4]:
+                if "spill stores" in nxt:
+                    w = nxt.replace(",", " ").split()
+                    sig["spill_stores"] = int(w[w.index("spill") - 2])
+                    sig["spill_loads"] = int(w[w.index("loads") - 3])
+                if "Used" in nxt and "registers" in nxt:
+                    w = nxt.split()
+                    sig["registers"] = int(w[w.index("registers,") - 1])
+            break
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    sig["sources_sha256"] = h.hexdigest()
+    return sig
 
 
 def measured_peaks():
@@ -319,10 +358,42 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
     return out
 
 
+def adjoint_summary(adj):
+    """The forward+adjoint cost and the finite-difference check in a few
+    numbers: per parameter, the relative difference of the adjoint and the
+    finite-difference totals and its z; the largest relative difference over
+    the aggregates (total, top, bottom) that the differences resolve (their
+    standard error under 2 %), at the step used for each parameter."""
+    out = {"ratio": round(adj["ratio"], 4), "fwd_ms": round(adj["fwd_ms"], 3),
+           "fwd_adjoint_ms": round(adj["fwd_adjoint_ms"], 3)}
+    fd = adj.get("fd_check")
+    if not fd:
+        return out
+    worst, worst_z = 0.0, 0.0
+    wide = fd.get("wide_step", {})
+    for q, name in enumerate(fd["params"]):
+        src, k = fd, q
+        if name in wide.get("params", []):
+            src, k = wide, wide["params"].index(name)
+        for agg in ("total", "top", "bottom"):
+            a = src[agg]
+            if a["fd_se"][k] < 0.02 * abs(a["fd"][k]):
+                worst = max(worst, a["rel_diff"][k])
+                worst_z = max(worst_z, a["z"][k])
+    out["fd"] = {"photons": fd["photons"], "h_rel": fd["h_rel"], "h_wide": wide.get("h_rel"),
+                 "wide_params": wide.get("params", []),
+                 "rel_diff_total": [round(x, 4) for x in fd["total"]["rel_diff"]],
+                 "z_total": [round(x, 2) for x in fd["total"]["z"]],
+                 "max_rel_diff_resolved": round(worst, 4), "max_z_resolved": round(worst_z, 2),
+                 "per_pmt_z": [None if z is None else round(z, 2) for z in fd["per_pmt"]["z"]],
+                 "rings_z_max": round(max(fd["rings"]["z_max"]), 2)}
+    return out
+
+
 def calibration_check():
     """The gradient calibration on the 50 cm TPC (64 point sources x 2e5
-    photons, hidden L_abs 30 m, L_Ray 35 cm, R_PTFE 0.97 / 0.80, start at the
-    defaults): recovered values, their standard deviations from the Fisher
+    photons on the nodes of a 5 cm 3-D grid in the LXe, hidden L_abs 30 m,
+    L_Ray 35 cm, R_PTFE 0.97 / 0.80, start at the defaults): recovered values, their standard deviations from the Fisher
     information, pulls, and the time per model launch."""
     import torch
     from paper_2203_14354_gb300 import calibrate, geometry, Tracker
@@ -331,7 +402,7 @@ def calibration_check():
     trk.set_adjoint([geometry.LXE], [0, 1])
     theta0 = trk.theta().tolist()
     truth = [30_000.0, 350.0, 0.97, 0.80]
-    ev = geometry.calibration_sources(200_000, n_x=8, n_z=8, spacing=50.0, z_center=-250.0)
+    ev = geometry.grid_sources(det, 200_000, 64, spacing=50.0, margin=50.0, seed=7)
     trk.upload_events(ev)
     target = calibrate.hit_maps(trk, truth, seed=7)
     cal = calibrate.Calibration(trk, ev, target, model_scale=2)
@@ -339,7 +410,7 @@ def calibration_check():
     rec = torch.tensor(res["theta"], dtype=torch.float64)
     sigma = cal.covariance(rec, seed=98).diagonal().sqrt()
     pull = (rec - torch.tensor(truth, dtype=torch.float64)) / sigma
-    return {"workload": "50 cm TPC, 64 point sources x 2e5 photons (model 2x), 4 parameters",
+    return {"workload": "50 cm TPC, 64 point sources x 2e5 photons on a 5 cm 3-D grid (model 2x), 4 parameters",
             "params": ["L_abs_LXe_mm", "L_ray_LXe_mm", "R_PTFE_LXe", "R_PTFE_GXe"], "truth": truth,
             "start": theta0, "recovered": res["theta"], "sigma": sigma.tolist(), "pull": pull.tolist(),
             "launches": res["launches"], "scoring_steps": res["scoring_steps"], "seconds": res["seconds"]}
@@ -364,7 +435,7 @@ def events_throughput(det, reps=3):
     trk.upload_events(ev[::10])
     sub = trk.alloc_event_results(256, hist=False)
     best, table = autotune_launch(trk, lambda: trk.propagate_events(seed=1, out=sub, hist=False, sync=False),
-                                  blocks=(3, 4, 5), chunks=(32, 64, 128), reps=2)
+                                  blocks=(3, 4, 5), chunks=(32, 64, 128), threads=(128, 256), reps=2)
     del sub
     trk.upload_events(ev)
     out = trk.alloc_event_results(256, hist=True)
@@ -395,8 +466,8 @@ def events_throughput(det, reps=3):
     return {"workload": "4096 S1 + 512 S2 events, DARWIN-scale mesh, one persistent launch under a CUDA graph, "
                         "per-event per-PMT counts + 257-bin histograms", "events": len(ev),
             "photons": trk.event_photons, "ms": ms, "photons_per_s": trk.event_photons / (ms / 1e3),
-            "launch": {"blocks_per_sm": best[0], "chunk": best[1]},
-            "autotune_ms": {f"{b}x{c}": round(t, 3) for (b, c), t in table.items()},
+            "launch": {"threads": best[0], "blocks_per_sm": best[1], "chunk": best[2]},
+            "autotune_ms": {f"{t}t x {b} x {c}": round(ms, 3) for (t, b, c), ms in table.items()},
             "lce": float(out["lce"].sum().item()) / trk.event_photons, "escaped": int(f[4]), "geom_err": int(f[6])}
 
 
@@ -531,6 +602,11 @@ def main():
     barrier()
     elapsed_ms = t_start.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in zip(k_start, k_end)]
+    if world > 1:
+        # the one collective of the photon-id split: the tallies of the last
+        # timed step summed over the ranks, checked against the photons run
+        from paper_2203_14354_gb300.shard import reduce_tallies
+        reduce_tallies(out)
     fates = out["fates"].cpu().numpy()
     lce = out["lce"].cpu().numpy()
     t90 = analysis.t90(out["hist"].cpu().numpy(), 1.0)
@@ -540,7 +616,8 @@ def main():
         elapsed_ms = float(t.item())
     ms_per_step = elapsed_ms / args.steps
     value = world * n * args.steps / (elapsed_ms / 1e3)
-
+    tallies = {"photons": world * n, "fates_sum": int(fates[:7].sum()), "reduced_over_ranks": world,
+               "ok": int(fates[:7].sum()) == world * n}
     # traversal work of the same batch (separate, untimed launch of the counting build)
     st_out = trk.alloc_results(1000)
     trk.propagate(n, base=base0 + args.warmup * n, seed=1, out=st_out, stats=True)
@@ -599,6 +676,25 @@ def main():
         cpu, _, _ = cpu_baseline(det, args.cpu_seconds)
 
     if rank == 0:
+        sig = kernel_signature()
+        stale = any(sig[k] != CAPTURED_KERNEL[k] for k in CAPTURED_KERNEL)
+        phases = dict(zip(("node_loop", "leaf_loop", "trav_setup", "draws", "interaction", "refill"),
+                          stats[29:35] / max(stats[29:35].sum(), 1.0)))
+        details = {
+            "roofline": {"per_step": {"nodes": nodes / steps_total, "leaves": leaves / steps_total,
+                                      "triangles": tris / steps_total, "ops": ops_per_step,
+                                      "fetch_bytes": bytes_per_step},
+                         "fetch": {"achieved_gbs": fetch_gbs, "hbm_peak_gbs": hbm, "frac_of_hbm": fetch_gbs / hbm},
+                         "simd_efficiency": simd, "lane_cycle_share": phases,
+                         "issue": {"warp_inst_per_step": WARP_INST_PER_STEP,
+                                   "achieved_g_warp_inst_s": issue_rate / 1e9,
+                                   "peak_g_warp_inst_s": issue_peak / 1e9, "frac": issue_rate / issue_peak},
+                         "kernel_signature": sig, "captured_kernel": CAPTURED_KERNEL},
+            "physics": {"fates": fates.tolist()}, "setup_s": setup_s, "bvh": dict(trk.bvh_info),
+            "adjoint": adjoint, "events": events, "spectral": spectral, "calibration": calibration,
+        }
+        print(json.dumps({"details": details}), flush=True)
+        r3 = lambda v: None if v is None else round(float(v), 4)   # noqa: E731
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -606,39 +702,31 @@ def main():
             "config": workload_config(n, world, det.n_tris),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "G lane-ops/s (FP32/INT32)", "frac": achieved / alu_peak,
-                         "traffic": DRAM_BYTES_PER_PHOTON * n if DRAM_BYTES_PER_PHOTON else None,
+                         "traffic": None if stale else DRAM_BYTES_PER_PHOTON * n, "stale": stale,
                          "peak_source": f"{N_SM} SMs x {LANES_PER_SM} lanes x sm_max_mhz ({peak_kind})",
-                         "algorithmic_ops": f"per photon step: {OPS_PER_NODE} per node visit + {OPS_PER_TRI} per "
-                                            f"triangle test + {OPS_PHYSICS} physics",
-                         "per_step": {"nodes": nodes / steps_total, "leaves": leaves / steps_total,
-                                      "triangles": tris / steps_total, "ops": ops_per_step,
-                                      "fetch_bytes": bytes_per_step},
-                         "fetch": {"achieved_gbs": fetch_gbs, "hbm_peak_gbs": hbm, "frac_of_hbm": fetch_gbs / hbm},
-                         "steps_per_photon": steps_total / n, "kernel_ms": statistics.mean(kern_ms),
-                         "simd_efficiency": simd,
-                         "issue": {"warp_inst_per_step": WARP_INST_PER_STEP,
-                                   "achieved_g_warp_inst_s": issue_rate / 1e9,
-                                   "peak_g_warp_inst_s": issue_peak / 1e9, "frac": issue_rate / issue_peak,
-                                   "source": "warp instructions per step from the ncu capture of this kernel"}},
+                         "ops_per_step": r3(ops_per_step), "kernel_ms": r3(statistics.mean(kern_ms)),
+                         "lanes_active": {k: r3(v) for k, v in simd.items()},
+                         "issue_frac": None if stale else r3(issue_rate / issue_peak)},
             "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * 1,
             "clocks": clk.summary(),
-            "physics": {"lce": float(lce.sum()) / n, "steps_per_photon": float(fates[7]) / n,
-                        "escaped": int(fates[4]), "geom_err": int(fates[6]), "truncated": int(fates[5]),
-                        "t90_ns": t90, "t90_nr_profile_ns": t90_nr},
-            "setup_s": setup_s, "bvh": {k: v for k, v in trk.bvh_info.items()},
+            "physics": {"lce": r3(float(lce.sum()) / (world * n)), "steps_per_photon": r3(float(fates[7]) / (world * n)),
+                        "escaped": int(fates[4]), "geom_err": int(fates[6]), "t90_ns": r3(t90),
+                        "t90_nr_profile_ns": r3(t90_nr), "tallies": tallies},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
-        if adjoint is not None:
-            line["adjoint"] = adjoint
         if events is not None:
-            line["events"] = events
+            line["events"] = {"photons_per_s": events["photons_per_s"], "ms": r3(events["ms"]),
+                              "launch": events["launch"]}
         if spectral is not None:
-            line["spectral"] = spectral
+            line["spectral"] = {"photons_per_s": spectral["photons_per_s"], "cost_ratio": r3(spectral["cost_ratio"])}
         if calibration is not None:
-            line["calibration"] = calibration
+            line["calibration"] = {"pull": [r3(x) for x in calibration["pull"]],
+                                   "launches": calibration["launches"]}
+        if adjoint is not None:
+            line["adjoint"] = adjoint_summary(adjoint)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -179,6 +179,9 @@ typedef struct {
 /* largest n_tbins (LXO_ERR_ARG above it) */
 #define LXO_MAX_TBINS (1u << 24)
 
+/* length of lxo_results.stats */
+#define LXO_STATS_LEN 40u
+
 /* run flags */
 #define LXO_FLAG_STATS 1u    /* count traversal work into lxo_results.stats (a separate kernel build) */
 #define LXO_FLAG_ADJOINT 2u  /* accumulate the adjoint tallies of detected photons into lxo_results.adjoint */
@@ -208,18 +211,25 @@ typedef struct {
     uint32_t* hist;              /* device [P*(n_tbins+1)]: detected arrival-time histogram (row = channel) */
     unsigned long long* fates;   /* device [8+M+S] */
     uint32_t* ph_fate;           /* optional device [n]: fate code per photon */
-    int32_t* ph_detail;          /* optional device [n]: channel / material / surface / triangle */
+    int32_t* ph_detail;          /* optional device [n]: channel (DETECTED, QE_FAIL), material (BULK_ABS),
+                                    surface (SURF_ABS), triangle (GEOM_ERR); -1 (ESCAPED, TRUNCATED) */
     uint32_t* ph_steps;          /* optional device [n] */
     float* ph_time;              /* optional device [n]: time at the end, ns */
     double* adjoint;             /* device [P*K] with LXO_FLAG_ADJOINT: per channel, sums over detected
                                     photons of their tallies (layout of lxo_set_adjoint) */
-    unsigned long long* stats;   /* device [32] with LXO_FLAG_STATS (accumulated): [0..3] photon steps,
-                                    BVH nodes visited, leaves visited, triangles tested (lane counts);
-                                    [4..6] warp iterations of the node loop, of the leaf loop and of
-                                    the photon loop; [7..8] lane cycles in traversal, in steps;
-                                    [9..17] steps in material 0 by nodes visited (bins of 8, last
-                                    >= 64), [18] their leaves; [19..28] the same for other
-                                    materials */
+    unsigned long long* stats;   /* device [LXO_STATS_LEN] with LXO_FLAG_STATS (accumulated): [0..3]
+                                    photon steps, BVH nodes visited, leaves visited, triangles tested
+                                    (lane counts); [4..6] warp iterations of the node loop, of the
+                                    leaf loop and of the photon loop; [7..8] lane cycles in
+                                    traversal, in steps; [9..17] steps in material 0 by nodes
+                                    visited (bins of 8, last >= 64), [18] their leaves; [19..28]
+                                    the same for other materials; [29..34] lane cycles in the node
+                                    loop, the leaf loop, the traversal set-up, the step's draws, the
+                                    interaction, and the refill (tallies, new photons) */
+    float* ph_state;             /* optional device [n*9]: per photon, its state when it met its fate
+                                    (or was cut by max_steps): position (mm), unit direction and unit
+                                    polarisation, 3 floats each -- so the outgoing wave of every
+                                    interaction can be checked photon by photon */
 } lxo_results;
 
 typedef struct {
@@ -307,9 +317,10 @@ lxo_status lxo_propagate_host(lxo_ctx* ctx, const lxo_source* src, uint64_t n, u
  * Many sources of uneven photon counts in one persistent launch (the
  * paper's LCE maps run ~2500 point sources, Sec. 4.1; S1 light from an
  * interaction point and S2 light along the electron path in the gas gap,
- * Sec. 1).  Event e's photon i has photon id (e << 32) | i, so its random
- * stream is that of a single-source lxo_propagate with
- * photon_id_base = e << 32, and each event is reproducible on its own. */
+ * Sec. 1).  Event e's photon i has photon id (e << 32) | i (e = the event
+ * id, see lxo_upload_events), so its random stream is that of a
+ * single-source lxo_propagate with photon_id_base = e << 32, and each event
+ * is reproducible on its own. */
 typedef struct {
     int32_t kind;         /* LXO_SRC_POINT, LXO_SRC_SEGMENT or LXO_SRC_BALL */
     int32_t medium;
@@ -327,8 +338,13 @@ typedef struct {
 } lxo_event;
 
 /* Copies the event table (host [n]) to the device (context-owned, replaces
- * the previous table).  Synchronous. */
-lxo_status lxo_upload_events(lxo_ctx* ctx, const lxo_event* ev, uint32_t n);
+ * the previous table).  Event e of the table has the event id
+ * first_event + e (its photons have ids ((first_event + e) << 32) | i);
+ * tallies still go to row e.  A job split into contiguous event ranges, one
+ * per GPU, each uploaded with its first event's id, therefore reproduces the
+ * single-GPU run's tallies row for row.  LXO_ERR_ARG if
+ * first_event + n > 2^32.  Synchronous. */
+lxo_status lxo_upload_events(lxo_ctx* ctx, const lxo_event* ev, uint32_t n, uint32_t first_event);
 
 /* Propagates every photon of the uploaded events in one launch.  out (device,
  * caller-owned, accumulated): lce, det [E*P] (row = event), hist
@@ -340,9 +356,12 @@ lxo_status lxo_upload_events(lxo_ctx* ctx, const lxo_event* ev, uint32_t n);
 lxo_status lxo_propagate_events(lxo_ctx* ctx, const lxo_run_params* params, const lxo_results* out, void* stream);
 
 /* Launch shape of the propagation kernels (found by an autotuner):
- * blocks_per_sm in 1..the occupancy limit (0 = the limit) and photon ids
- * taken per warp from the work queue, chunk in 1..4096 (0 = 64). */
-lxo_status lxo_set_launch(lxo_ctx* ctx, uint32_t blocks_per_sm, uint32_t chunk);
+ * threads per block, 128 or 256 (0 = 256; each has its own kernel build
+ * with the same registers per thread, and 256 is used for LXO_FLAG_STATS);
+ * blocks_per_sm in 1..the occupancy limit (0 = the limit; the limit is 5
+ * blocks of 256 or 10 of 128); photon ids taken per warp from the work
+ * queue, chunk in 1..4096 (0 = 64).  Results do not depend on the shape. */
+lxo_status lxo_set_launch(lxo_ctx* ctx, uint32_t blocks_per_sm, uint32_t chunk, uint32_t threads);
 
 /* Adjoint (an extension of the paper's method: it has no gradients; the
  * quantities are its Table 2 parameters and the Sec. 2.1 electrode model).
@@ -405,7 +424,10 @@ lxo_status lxo_sync(lxo_ctx* ctx, void* stream);
  *    corrupt each other's results.  Synchronous.
  *  - On success it allocates nothing, on the device or the host; the
  *    messages of its own argument checks are cut to the context string's
- *    current capacity. */
+ *    current capacity.
+ *  - A fault flagged by the kernel returns LXO_ERR_DEVICE (the flag word in
+ *    the message, as lxo_sync reports it) and leaves the host arrays as they
+ *    were. */
 lxo_status lxo_propagate_host_static(lxo_ctx* ctx, const lxo_source* src, uint64_t n, uint64_t photon_id_base,
                                      const lxo_run_params* params, const lxo_results* host_out, void* stream);
 

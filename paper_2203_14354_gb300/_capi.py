@@ -20,6 +20,7 @@ LXO_FLAG_ADJOINT = 2
 LXO_STATIC_SCRATCH_BYTES = 8 << 20
 LXO_REF_WAVELENGTH_NM = 175.0
 LXO_MAX_TBINS = 1 << 24
+LXO_STATS_LEN = 40
 FATE_NAMES = ["detected", "qe_fail", "bulk_abs", "surf_abs", "escaped", "truncated", "geom_err"]
 
 
@@ -61,7 +62,8 @@ class lxo_run_params(C.Structure):
 class lxo_results(C.Structure):
     _fields_ = [("lce", C.c_void_p), ("det", C.c_void_p), ("hist", C.c_void_p), ("fates", C.c_void_p),
                 ("ph_fate", C.c_void_p), ("ph_detail", C.c_void_p), ("ph_steps", C.c_void_p),
-                ("ph_time", C.c_void_p), ("adjoint", C.c_void_p), ("stats", C.c_void_p)]
+                ("ph_time", C.c_void_p), ("adjoint", C.c_void_p), ("stats", C.c_void_p),
+                ("ph_state", C.c_void_p)]
 
 
 class lxo_bvh_info(C.Structure):
@@ -94,9 +96,9 @@ _SIGNATURES = {
                                      C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
     "lxo_sync": (C.c_int, [vp, vp]),
     "lxo_set_adjoint": (C.c_int, [vp, vp, C.c_uint32, vp, C.c_uint32]),
-    "lxo_upload_events": (C.c_int, [vp, vp, C.c_uint32]),
+    "lxo_upload_events": (C.c_int, [vp, vp, C.c_uint32, C.c_uint32]),
     "lxo_propagate_events": (C.c_int, [vp, C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),
-    "lxo_set_launch": (C.c_int, [vp, C.c_uint32, C.c_uint32]),
+    "lxo_set_launch": (C.c_int, [vp, C.c_uint32, C.c_uint32, C.c_uint32]),
     "lxo_adjoint_jacobian": (C.c_int, [vp, vp, C.c_uint32, vp, vp, vp, vp]),
     "lxo_propagate_host_static": (C.c_int, [vp, C.POINTER(lxo_source), C.c_uint64, C.c_uint64,
                                             C.POINTER(lxo_run_params), C.POINTER(lxo_results), vp]),

@@ -255,14 +255,20 @@ def main(argv=None):
     ap.add_argument("--model-scale", type=int, default=2)
     ap.add_argument("--truth", type=float, nargs=4, default=(30_000.0, 350.0, 0.97, 0.80))
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--layout", choices=("grid3d", "plane"), default="grid3d",
+                    help="sources on a seeded subset of the 3-D grid nodes in the active LXe (default), or on a "
+                         "grid in the plane y = 0")
     a = ap.parse_args(argv)
     t_build = time.perf_counter()
     if a.detector == "darwin":
         det = g.darwin()
-        events = g.calibration_sources(a.photons)
+        events = (g.grid_sources(det, a.photons, 256, spacing=100.0, margin=50.0, seed=a.seed)
+                  if a.layout == "grid3d" else g.calibration_sources(a.photons))
     else:
         det = g.scaled_tpc()
-        events = g.calibration_sources(a.photons, n_x=8, n_z=8, spacing=50.0, z_center=-250.0)
+        events = (g.grid_sources(det, a.photons, 64, spacing=50.0, margin=50.0, seed=a.seed)
+                  if a.layout == "grid3d" else
+                  g.calibration_sources(a.photons, n_x=8, n_z=8, spacing=50.0, z_center=-250.0))
     trk = Tracker(det)
     t_build = time.perf_counter() - t_build
     trk.set_adjoint([g.LXE], [0, 1])
@@ -277,7 +283,8 @@ def main(argv=None):
     sigma = cal.covariance(res["theta"], seed=a.seed + 2).diagonal().sqrt().tolist()
     photons_per_iter = sum(n for _, n in events) * a.model_scale
     print(json.dumps(dict(
-        detector=a.detector, sources=len(events), photons_per_source=a.photons, model_scale=a.model_scale,
+        detector=a.detector, layout=a.layout, sources=len(events), photons_per_source=a.photons,
+        model_scale=a.model_scale,
         params=["L_abs_LXe_mm", "L_ray_LXe_mm", "R_PTFE_LXe", "R_PTFE_GXe"],
         truth=list(a.truth), start=theta0, recovered=res["theta"],
         rel_error=[(r - t) / t for r, t in zip(res["theta"], a.truth)], sigma=sigma,

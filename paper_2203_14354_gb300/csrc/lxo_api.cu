@@ -33,10 +33,11 @@ struct lxo_ctx {
     std::vector<lxo_pmt> pmts;
     std::vector<int32_t> adj_mats, adj_surfs;
     std::vector<lxo_event> events;
-    uint32_t launch_blocks_per_sm = 0, launch_chunk = 64;
+    uint32_t launch_blocks_per_sm = 0, launch_chunk = 64, launch_threads = 256;
     // device
     lxo::EventDev* d_events = nullptr;
     unsigned long long* d_ev_prefix = nullptr;
+    uint32_t first_event = 0;   // event id of the table's first event
     uint64_t ev_total = 0;
     float4* d_nodes = nullptr;
     float4* d_tris = nullptr;
@@ -246,6 +247,7 @@ lxo_status fill_params(lxo_ctx* c, const lxo_source* src, uint64_t n, uint64_t b
     p->err = c->d_err;
     p->chunk = c->launch_chunk;
     p->blocks_per_sm = c->launch_blocks_per_sm;
+    p->block_threads = c->launch_threads;
     for (int m = 0; m < LXO_MAX_MATERIALS; ++m) p->adj_mat_slot[m] = -1;
     for (int q = 0; q < LXO_MAX_SURFACES; ++q) p->adj_surf_slot[q] = -1;
     p->adj_k = 0;
@@ -544,8 +546,8 @@ lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uin
     if (!rp) return fail(c, LXO_ERR_ARG, "propagate_host: run params are NULL");
     if (!host_out || !host_out->lce || !host_out->det || !host_out->hist || !host_out->fates)
         return fail(c, LXO_ERR_ARG, "propagate_host: lce, det, hist and fates buffers are required");
-    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->stats ||
-        host_out->adjoint)
+    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->ph_state ||
+        host_out->stats || host_out->adjoint)
         return fail(c, LXO_ERR_ARG, "propagate_host: per-photon outputs, stats and adjoint are device-only");
     if (rp->flags & (LXO_FLAG_STATS | LXO_FLAG_ADJOINT))
         return fail(c, LXO_ERR_ARG, "propagate_host: LXO_FLAG_STATS / LXO_FLAG_ADJOINT not supported");
@@ -584,11 +586,13 @@ lxo_status lxo_propagate_host(lxo_ctx* c, const lxo_source* src, uint64_t n, uin
     return LXO_OK;
 }
 
-lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n)
+lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n, uint32_t first_event)
 {
     NvtxRange nvtx("lxo_upload_events");
     if (!c) return LXO_ERR_ARG;
     if (!ev || n == 0) return fail(c, LXO_ERR_ARG, "upload_events: no events");
+    if ((uint64_t)first_event + n > (1ull << 32))
+        return fail(c, LXO_ERR_ARG, "upload_events: event ids %u + %u exceed 2^32", first_event, n);
     std::vector<lxo::EventDev> h(n);
     std::vector<unsigned long long> pre(n + 1, 0);
     for (uint32_t e = 0; e < n; ++e) {
@@ -624,6 +628,7 @@ lxo_status lxo_upload_events(lxo_ctx* c, const lxo_event* ev, uint32_t n)
        "upload_events: copy");
     c->events.assign(ev, ev + n);
     c->ev_total = pre[n];
+    c->first_event = first_event;
     return LXO_OK;
 }
 
@@ -637,7 +642,8 @@ lxo_status lxo_propagate_events(lxo_ctx* c, const lxo_run_params* rp, const lxo_
     if (!rp) return fail(c, LXO_ERR_ARG, "propagate_events: run params are NULL");
     if (!out || !out->lce || !out->det || !out->fates)
         return fail(c, LXO_ERR_ARG, "propagate_events: lce, det and fates buffers are required");
-    if (out->ph_fate || out->ph_detail || out->ph_steps || out->ph_time || out->stats || (rp->flags & LXO_FLAG_STATS))
+    if (out->ph_fate || out->ph_detail || out->ph_steps || out->ph_time || out->ph_state || out->stats ||
+        (rp->flags & LXO_FLAG_STATS))
         return fail(c, LXO_ERR_ARG, "propagate_events: per-photon outputs and stats are not supported");
     if ((rp->flags & LXO_FLAG_ADJOINT) && !out->adjoint)
         return fail(c, LXO_ERR_ARG, "propagate_events: LXO_FLAG_ADJOINT needs the adjoint buffer");
@@ -659,6 +665,7 @@ lxo_status lxo_propagate_events(lxo_ctx* c, const lxo_run_params* rp, const lxo_
         }
     p.out = *out;
     p.n_events = (uint32_t)c->events.size();
+    p.first_event = c->first_event;
     p.events = c->d_events;
     p.ev_prefix = c->d_ev_prefix;
     if (c->ev_total == 0) return LXO_OK;
@@ -669,12 +676,16 @@ lxo_status lxo_propagate_events(lxo_ctx* c, const lxo_run_params* rp, const lxo_
     return LXO_OK;
 }
 
-lxo_status lxo_set_launch(lxo_ctx* c, uint32_t blocks_per_sm, uint32_t chunk)
+lxo_status lxo_set_launch(lxo_ctx* c, uint32_t blocks_per_sm, uint32_t chunk, uint32_t threads)
 {
     if (!c) return LXO_ERR_ARG;
-    if (blocks_per_sm > 32 || chunk > 4096) return fail(c, LXO_ERR_ARG, "set_launch: blocks_per_sm <= 32, chunk <= 4096");
+    if (blocks_per_sm > 32 || chunk > 4096)
+        return fail(c, LXO_ERR_ARG, "set_launch: blocks_per_sm <= 32, chunk <= 4096");
+    if (threads != 0 && threads != 128 && threads != 256)
+        return fail(c, LXO_ERR_ARG, "set_launch: threads per block 128 or 256 (0 = 256), not %u", threads);
     c->launch_blocks_per_sm = blocks_per_sm;
     c->launch_chunk = chunk ? chunk : 64;
+    c->launch_threads = threads ? threads : 256;
     return LXO_OK;
 }
 
@@ -790,8 +801,8 @@ extern "C" lxo_status lxo_propagate_host_static(lxo_ctx* c, const lxo_source* sr
     if (!rp) return static_fail(c, LXO_ERR_ARG, "run params are NULL");
     if (!host_out || !host_out->lce || !host_out->det || !host_out->hist || !host_out->fates)
         return static_fail(c, LXO_ERR_ARG, "lce, det, hist, fates host buffers required");
-    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->stats ||
-        host_out->adjoint || (rp->flags & (LXO_FLAG_STATS | LXO_FLAG_ADJOINT)))
+    if (host_out->ph_fate || host_out->ph_detail || host_out->ph_steps || host_out->ph_time || host_out->ph_state ||
+        host_out->stats || host_out->adjoint || (rp->flags & (LXO_FLAG_STATS | LXO_FLAG_ADJOINT)))
         return static_fail(c, LXO_ERR_ARG, "per-photon outputs, stats and adjoint unsupported");
     lxo_status s = validate(c);
     if (s) return s;
@@ -802,8 +813,8 @@ extern "C" lxo_status lxo_propagate_host_static(lxo_ctx* c, const lxo_source* sr
     const uint64_t need = hist_off + 4 * P * B;
     if (B > (1ull << 32) || need > (uint64_t)LXO_STATIC_SCRATCH_BYTES)
         return static_fail(c, LXO_ERR_ARG, "tallies exceed LXO_STATIC_SCRATCH_BYTES");
-    DeviceGuard g(c->device);
     if (c->device < 0 || c->device >= kMaxStaticDevices) return static_fail(c, LXO_ERR_ARG, "device index");
+    DeviceGuard g(c->device);
     unsigned char* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_static_mu);
@@ -834,14 +845,23 @@ extern "C" lxo_status lxo_propagate_host_static(lxo_ctx* c, const lxo_source* sr
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.out.det, host_out->det, 4 * P, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.out.hist, host_out->hist, 4 * P * B, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && n > 0) e = lxo::launch_propagate(p, c->device, st);
+    // the fault flags first: on a fault the caller's arrays stay untouched,
+    // as with lxo_propagate_host
     int herr = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->fates, p.out.fates, 8 * NF, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->lce, p.out.lce, 4 * P, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->det, p.out.det, 4 * P, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->hist, p.out.hist, 4 * P * B, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, p.err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return static_fail(c, LXO_ERR_CUDA, cudaGetErrorString(e));
-    if (herr) return static_fail(c, LXO_ERR_DEVICE, "device fault flags set");
+    if (herr) {
+        char msg[128];  // on the stack: the message allocates nothing
+        snprintf(msg, sizeof msg,
+                 "device fault flags 0x%x (1 = traversal stack, 2 = channel range, 8 = index out of range)", herr);
+        return static_fail(c, LXO_ERR_DEVICE, msg);
+    }
+    e = cudaMemcpyAsync(host_out->fates, p.out.fates, 8 * NF, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->lce, p.out.lce, 4 * P, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->det, p.out.det, 4 * P, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out->hist, p.out.hist, 4 * P * B, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return static_fail(c, LXO_ERR_CUDA, cudaGetErrorString(e));
     return LXO_OK;
 }

@@ -156,10 +156,12 @@ struct PropParams {
     signed char adj_surf_slot[LXO_MAX_SURFACES]; // tracked surface -> index, -1 if not
     int adj_n_mats;
     uint32_t n_events;                 // 0: single source
+    uint32_t first_event;              // event id of events[0]: photon ids ((first_event + e) << 32) | i
     const EventDev* events;            // [n_events]
     const unsigned long long* ev_prefix;  // [n_events + 1] photon-count prefix sums
     uint32_t chunk;                    // photon ids per warp grab
     uint32_t blocks_per_sm;            // 0 = occupancy limit
+    uint32_t block_threads;            // threads per CTA of the propagation kernel: 128 or 256 (0 = 256)
     unsigned long long* queue;   // scratch: work-queue head
     int* err;                    // scratch: device error word
 };

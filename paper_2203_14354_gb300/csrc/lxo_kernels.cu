@@ -37,7 +37,6 @@ namespace lxo {
 #ifndef LXO_CHECK_BOUNDS
 #define LXO_CHECK_BOUNDS 0
 #endif
-constexpr int kPropThreadsK = 256;  // threads per CTA of the propagation kernel (stride of the adjoint tallies)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
@@ -183,10 +182,16 @@ __device__ __forceinline__ float safe_inv(float d)
     return __frcp_rn(fabsf(d) < 1e-20f ? copysignf(1e-20f, d) : d);
 }
 
+// lane cycles by phase of the photon loop (counting build): node loop, leaf
+// loop, traversal set-up, step draws, interaction, refill (tallies and new
+// photons)
+enum { kCycNode = 0, kCycLeaf, kCycBegin, kCycDraw, kCycFinish, kCycRefill, kCycPhases };
+
 struct Counters {
     uint32_t nodes, leaves, tris;
     uint32_t node_iters, leaf_iters;   // warp iterations of the node / leaf loops (counted by one lane)
     unsigned long long trav_cycles;     // lane cycles inside the traversal
+    unsigned long long cyc[kCycPhases];
 };
 
 __device__ __forceinline__ bool warp_leader()
@@ -303,6 +308,7 @@ __device__ void trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
     int node = ts.node, leaf = ts.leaf, sp = ts.sp;
     float bt = ts.bt;
     uint32_t best = ts.best, best_rec = ts.best_rec;
+    long long tq = kStats ? clock64() : 0;
     while (true) {
         while (node >= 0) {
             if (kStats) {
@@ -356,6 +362,11 @@ __device__ void trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
             leaf = node;
             node = stack[--sp];
         }
+        if (kStats) {
+            const long long t1 = clock64();
+            cnt.cyc[kCycNode] += (unsigned long long)(t1 - tq);
+            tq = t1;
+        }
         while (leaf != 0) {
             if (kStats && warp_leader()) cnt.leaf_iters++;
             test_leaf<kStats>(sc, ts.wr, leaf, ts.skip, bt, best, best_rec, cnt, err);
@@ -364,6 +375,11 @@ __device__ void trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
                 leaf = node;
                 node = stack[--sp];
             }
+        }
+        if (kStats) {
+            const long long t1 = clock64();
+            cnt.cyc[kCycLeaf] += (unsigned long long)(t1 - tq);
+            tq = t1;
         }
         if (node == kDone) break;
     }
@@ -385,7 +401,9 @@ __device__ Hit closest_hit(const Scene& sc, float3 o, float3 d, uint32_t skip, f
 {
     TravState ts;
     int stack[kStackSize];
+    const long long t0 = kStats ? clock64() : 0;
     trav_begin(sc, o, d, skip, tmax, ts, stack);
+    if (kStats) cnt.cyc[kCycBegin] += (unsigned long long)(clock64() - t0);
     trav_run<kStats>(sc, ts, stack, err, cnt);
     return trav_result(ts);
 }
@@ -486,7 +504,7 @@ __device__ Photon make_event_photon(const PropParams& p, uint64_t idx)
     }
     const EventDev ev = p.events[lo];
     Photon ph;
-    ph.pid = ((uint64_t)lo << 32) | (uint64_t)(idx - __ldg(&p.ev_prefix[lo]));
+    ph.pid = ((uint64_t)(p.first_event + lo) << 32) | (uint64_t)(idx - __ldg(&p.ev_prefix[lo]));
     ph.medium = ev.medium;
     ph.time = ev.t0 + emission_delay(p, ph.pid, ev.prof);
     ph.wl = p.spectral ? emission_wavelength(p, ph.pid, ev.spec) : 0.0f;
@@ -735,7 +753,7 @@ __device__ __forceinline__ void step_histogram(const PropParams& p, const Photon
 // Second half of a step: the interaction at the closest hit or in the bulk.
 // Returns -1 if the photon lives on, else its fate code (detail set to
 // channel / material / surface / triangle).
-// Adjoint tallies of one lane live in shared memory, tally k at tl[k * kPropThreads].
+// Adjoint tallies of one lane live in shared memory, tally k at tl[k * blockDim.x].
 constexpr int kAdjMaxK = 2 * (LXO_ADJ_MAX_MATERIALS + LXO_ADJ_MAX_SURFACES);
 
 template <bool kAdjoint, bool kSpectral>
@@ -753,12 +771,12 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
         }
         ph.pos = ph.pos + d_int * ph.dir;
         ph.time += d_int * n_over_c_at<kSpectral>(mt, ph.wl);
-        if (kAdjoint && ms >= 0) tl[(2 * ms) * kPropThreadsK] += d_int;
+        if (kAdjoint && ms >= 0) tl[(2 * ms) * blockDim.x] += d_int;
         if (d_abs <= d_ray) {
             detail = ph.medium;
             return LXO_FATE_BULK_ABS;
         }
-        if (kAdjoint && ms >= 0) tl[(2 * ms + 1) * kPropThreadsK] += 1.0f;
+        if (kAdjoint && ms >= 0) tl[(2 * ms + 1) * blockDim.x] += 1.0f;
         rayleigh(ph, p.seed);
         ph.last = LXO_NO_HIT;
         return -1;
@@ -766,7 +784,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
     const float3 o_ray = ph.pos;
     ph.pos = ph.pos + h.t * ph.dir;
     ph.time += h.t * n_over_c_at<kSpectral>(mt, ph.wl);
-    if (kAdjoint && ms >= 0) tl[(2 * ms) * kPropThreadsK] += h.t;
+    if (kAdjoint && ms >= 0) tl[(2 * ms) * blockDim.x] += h.t;
     // geometric normal and attributes of the triangle hit (record in leaf order)
     if (LXO_CHECK_BOUNDS && h.rec >= p.sc.n_records) {
         atomicOr(p.err, kErrBounds);
@@ -819,7 +837,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
             detail = (int)sid;
             return LXO_FATE_SURF_ABS;
         }
-        if (kAdjoint && ss >= 0) tl[base_k * kPropThreadsK] += 1.0f;
+        if (kAdjoint && ss >= 0) tl[base_k * blockDim.x] += 1.0f;
         specular = u.u3 < sf.spec;
     } else if (sf.type == LXO_SURF_ELECTRODE_T) {
         if (u.u2 < sf.T) {
@@ -827,7 +845,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
                 detail = (int)h.id;
                 return LXO_FATE_GEOM_ERR;
             }
-            if (kAdjoint && ss >= 0) tl[base_k * kPropThreadsK] += 1.0f;
+            if (kAdjoint && ss >= 0) tl[base_k * blockDim.x] += 1.0f;
             ph.medium = to;
             spawn_offset(ph, o_ray, h.t, Nf, -1.0f);
             return -1;
@@ -836,7 +854,7 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
             detail = (int)sid;
             return LXO_FATE_SURF_ABS;
         }
-        if (kAdjoint && ss >= 0) tl[(base_k + 1) * kPropThreadsK] += 1.0f;
+        if (kAdjoint && ss >= 0) tl[(base_k + 1) * blockDim.x] += 1.0f;
         specular = draw4(p.seed, ph.pid, ph.step, 1).u3 < sf.wspec;
     } else {
         detail = (int)h.id;
@@ -854,21 +872,25 @@ __device__ int finish_step(const PropParams& p, Photon& ph, const StepDraw& sd, 
 template <bool kStats, bool kAdjoint, bool kSpectral>
 __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counters& cnt, float* tl)
 {
+    const long long cd = kStats ? clock64() : 0;
     const StepDraw sd = begin_step<kSpectral>(p, ph);
     const long long c0 = kStats ? clock64() : 0;
+    if (kStats) cnt.cyc[kCycDraw] += (unsigned long long)(c0 - cd);
     const uint32_t n0 = kStats ? cnt.nodes : 0, l0 = kStats ? cnt.leaves : 0;
     const Hit h = closest_hit<kStats>(p.sc, ph.pos, ph.dir, ph.last, fminf(sd.d_abs, sd.d_ray), p.err, cnt);
     if (kStats) {
         cnt.trav_cycles += (unsigned long long)(clock64() - c0);
         step_histogram<kStats>(p, ph, cnt.nodes - n0, cnt.leaves - l0);
     }
-    return finish_step<kAdjoint, kSpectral>(p, ph, sd, h, detail, tl);
+    const long long cf = kStats ? clock64() : 0;
+    const int fate = finish_step<kAdjoint, kSpectral>(p, ph, sd, h, detail, tl);
+    if (kStats) cnt.cyc[kCycFinish] += (unsigned long long)(clock64() - cf);
+    return fate;
 }
 
 // ---------------------------------------------------------------------------
 // persistent propagation kernel
 // ---------------------------------------------------------------------------
-constexpr int kPropThreads = kPropThreadsK;
 // tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
 // idle; 5 CTAs of 256 threads per SM (48 registers) hide more L1/L2 latency
 // than 3 CTAs at 80 registers (+22 %) despite a few spills
@@ -889,8 +911,9 @@ template <bool kAdjoint>
 __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s_f, const Photon& ph, int fate,
                                       int detail, const float* tl)
 {
-    // row of the per-channel tallies: the channel, or event * P + channel for batched events
-    const size_t row = p.n_events ? (size_t)(ph.pid >> 32) * p.n_chan + detail : (size_t)detail;
+    // row of the per-channel tallies: the channel, or (event - first event) * P + channel for batched events
+    const size_t row = p.n_events ? (size_t)((uint32_t)(ph.pid >> 32) - p.first_event) * p.n_chan + detail
+                                  : (size_t)detail;
     if (LXO_CHECK_BOUNDS && (fate == LXO_FATE_DETECTED || fate == LXO_FATE_QE_FAIL) &&
         (detail < 0 || row >= (size_t)(p.n_events ? p.n_events : 1) * p.n_chan)) {
         atomicOr(p.err, kErrBounds);
@@ -898,7 +921,7 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
     }
     if (kAdjoint && fate == LXO_FATE_DETECTED)
         for (int k = 0; k < p.adj_k; ++k)
-            atomicAdd(&p.out.adjoint[row * p.adj_k + k], (double)tl[k * kPropThreads]);
+            atomicAdd(&p.out.adjoint[row * p.adj_k + k], (double)tl[k * blockDim.x]);
     atomicAdd(&s_f[fate], 1ull);
     atomicAdd(&s_f[7], (unsigned long long)ph.step);
     if (fate == LXO_FATE_BULK_ABS) atomicAdd(&s_f[LXO_FATES_FIXED + detail], 1ull);
@@ -919,6 +942,12 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
     if (p.out.ph_detail) p.out.ph_detail[idx] = detail;
     if (p.out.ph_steps) p.out.ph_steps[idx] = ph.step;
     if (p.out.ph_time) p.out.ph_time[idx] = ph.time;
+    if (p.out.ph_state) {
+        float* o = p.out.ph_state + 9 * idx;
+        o[0] = ph.pos.x; o[1] = ph.pos.y; o[2] = ph.pos.z;
+        o[3] = ph.dir.x; o[4] = ph.dir.y; o[5] = ph.dir.z;
+        o[6] = ph.pol.x; o[7] = ph.pol.y; o[8] = ph.pol.z;
+    }
 }
 
 // Persistent photon loop.  A lane whose photon reached its fate stays idle
@@ -927,14 +956,17 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
 // from a warp-local chunk (ballot + prefix popcount), chunks of p.chunk ids
 // coming from the global work-queue head.  Source sampling and tallies thus
 // run on many lanes at once instead of one lane per iteration.
-template <bool kStats, bool kAdjoint, bool kSpectral>
-__global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(const __grid_constant__ PropParams p)
+// Built for CTAs of kThreads = 256 (LXO_MIN_BLOCKS per SM) or 128 threads
+// (twice as many CTAs): the same register budget per thread either way.
+template <bool kStats, bool kAdjoint, bool kSpectral, int kThreads>
+__global__ void __launch_bounds__(kThreads, kThreads >= 256 ? LXO_MIN_BLOCKS : 2 * LXO_MIN_BLOCKS)
+    k_propagate(const __grid_constant__ PropParams p)
 {
     Counters cnt{};
     uint32_t my_steps = 0, outer_iters = 0;
     unsigned long long loop_cycles = 0;
     __shared__ unsigned long long s_f[kMaxFates];
-    __shared__ float s_tl[kAdjoint ? kAdjMaxK * kPropThreads : 1];
+    __shared__ float s_tl[kAdjoint ? kAdjMaxK * kThreads : 1];
     float* tl = kAdjoint ? &s_tl[threadIdx.x] : nullptr;
     for (int i = threadIdx.x; i < p.n_fates; i += blockDim.x) s_f[i] = 0ull;
     __syncthreads();
@@ -950,6 +982,7 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
     while (true) {
         uint32_t need = __ballot_sync(FULL_MASK, !alive);
         const int idle = __popc(need);
+        const long long cr = kStats ? clock64() : 0;
         if (idle >= LXO_REFILL_MIN || idle == 32) {
             if (pending) {
                 tally<kAdjoint>(p, s_f, ph, fate, detail, tl);
@@ -973,13 +1006,14 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
                 if (((need >> lane) & 1u) && rank < take) {
                     ph = make_photon(p, chunk_next + rank);
                     if (kAdjoint)
-                        for (int k = 0; k < p.adj_k; ++k) tl[k * kPropThreads] = 0.0f;
+                        for (int k = 0; k < p.adj_k; ++k) tl[k * kThreads] = 0.0f;
                     alive = true;
                 }
                 chunk_next += take;
                 need = __ballot_sync(FULL_MASK, !alive);
             }
         }
+        if (kStats) cnt.cyc[kCycRefill] += (unsigned long long)(clock64() - cr);
         if (!__any_sync(FULL_MASK, alive || pending)) break;
         if (kStats && lane == 0) outer_iters++;
         const long long c0 = kStats ? clock64() : 0;
@@ -987,7 +1021,10 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
             fate = photon_step<kStats, kAdjoint, kSpectral>(p, ph, detail, cnt, tl);
             ph.step++;
             if (kStats) my_steps++;
-            if (fate < 0 && ph.step >= p.max_steps) fate = LXO_FATE_TRUNCATED;
+            if (fate < 0 && ph.step >= p.max_steps) {
+                fate = LXO_FATE_TRUNCATED;
+                detail = -1;
+            }
             if (fate >= 0) {
                 alive = false;
                 pending = true;
@@ -1008,6 +1045,7 @@ __global__ void __launch_bounds__(kPropThreads, LXO_MIN_BLOCKS) k_propagate(cons
         atomicAdd(&p.out.stats[6], (unsigned long long)outer_iters);
         atomicAdd(&p.out.stats[7], cnt.trav_cycles);
         atomicAdd(&p.out.stats[8], loop_cycles);
+        for (int k = 0; k < kCycPhases; ++k) atomicAdd(&p.out.stats[29 + k], cnt.cyc[k]);
     }
 }
 
@@ -1033,26 +1071,35 @@ cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
+template <int kThreads>
+static cudaError_t launch_propagate_t(const PropParams& p, int sms, cudaStream_t st)
 {
-    if (p.n == 0) return cudaSuccess;
-    int sms = 0, per_sm = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (e != cudaSuccess) return e;
     const bool stats = (p.flags & LXO_FLAG_STATS) != 0;
     const bool adj = (p.flags & LXO_FLAG_ADJOINT) != 0;
-    auto kern = p.spectral ? (stats ? (adj ? k_propagate<true, true, true> : k_propagate<true, false, true>)
-                                    : (adj ? k_propagate<false, true, true> : k_propagate<false, false, true>))
-                           : (stats ? (adj ? k_propagate<true, true, false> : k_propagate<true, false, false>)
-                                    : (adj ? k_propagate<false, true, false> : k_propagate<false, false, false>));
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPropThreads, 0);
+    auto kern = p.spectral ? (adj ? k_propagate<false, true, true, kThreads> : k_propagate<false, false, true, kThreads>)
+                           : (adj ? k_propagate<false, true, false, kThreads> : k_propagate<false, false, false, kThreads>);
+    if (stats)  // the counting build exists for the default block size only
+        kern = p.spectral ? (adj ? k_propagate<true, true, true, 256> : k_propagate<true, false, true, 256>)
+                          : (adj ? k_propagate<true, true, false, 256> : k_propagate<true, false, false, 256>);
+    const int threads = stats ? 256 : kThreads;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
     if (e != cudaSuccess) return e;
     if (p.blocks_per_sm > 0 && (int)p.blocks_per_sm < per_sm) per_sm = (int)p.blocks_per_sm;
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    const uint64_t need = (p.n + kPropThreads - 1) / kPropThreads;
+    const uint64_t need = (p.n + threads - 1) / threads;
     if (need < blocks) blocks = need;
-    kern<<<(unsigned)blocks, kPropThreads, 0, st>>>(p);
+    kern<<<(unsigned)blocks, threads, 0, st>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
+{
+    if (p.n == 0) return cudaSuccess;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    return p.block_threads == 128 ? launch_propagate_t<128>(p, sms, st) : launch_propagate_t<256>(p, sms, st);
 }
 
 // ---------------------------------------------------------------------------

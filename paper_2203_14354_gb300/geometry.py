@@ -1079,3 +1079,38 @@ def calibration_sources(n_photons, n_x=16, n_z=16, spacing=100.0, z_center=-1299
     xs = (np.arange(n_x) - (n_x - 1) / 2.0) * spacing
     zs = z_center + (np.arange(n_z) - (n_z - 1) / 2.0) * spacing
     return [(Source(SRC_POINT, medium, center=(float(x), 0.0, float(z))), int(n_photons)) for z in zs for x in xs]
+
+
+def grid_sources(det, n_photons, n_sources=256, spacing=100.0, margin=50.0, seed=0, medium=LXE):
+    """Point sources for a calibration fit on a 3-D grid: the nodes of a
+    cubic grid of pitch ``spacing`` (mm, aligned with the origin) inside the
+    detector's active volume -- the regular-polygon prism of its volume
+    source (the LXe between cathode and gate inside the wall) -- at least
+    ``margin`` mm from every wall side and from the prism's bottom and top;
+    a seeded random subset of ``n_sources`` of them (all if fewer), each
+    emitting ``n_photons``.  The DARWIN-scale detector has about 12 000 such
+    nodes at 10 cm.  Returns a list of (Source, n_photons), ordered by
+    (z, y, x)."""
+    s = det.source
+    if s.kind != SRC_VOLUME_POLYGON:
+        raise ValueError("grid_sources needs a detector whose source is its active volume (a polygon prism)")
+    n = max(int(s.n_sides), 3) if s.n_sides else 0
+    r_out = float(s.radius)
+    ext = r_out + spacing
+    ax = np.arange(np.floor(-ext / spacing), np.ceil(ext / spacing) + 1) * spacing
+    az = np.arange(np.ceil((s.z_min + margin) / spacing), np.floor((s.z_max - margin) / spacing) + 1) * spacing
+    z, y, x = np.meshgrid(az, ax, ax, indexing="ij")
+    x, y, z = x.ravel(), y.ravel(), z.ravel()
+    if n:
+        apothem = r_out * math.cos(math.pi / n)
+        ok = np.ones(x.size, bool)
+        for k in range(n):   # side k's outward normal, half-way between vertices k and k + 1
+            a = s.phase + 2.0 * math.pi * (k + 0.5) / n
+            ok &= x * math.cos(a) + y * math.sin(a) <= apothem - margin
+    else:
+        ok = x * x + y * y <= (r_out - margin) ** 2
+    x, y, z = x[ok], y[ok], z[ok]
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(x.size, min(n_sources, x.size), replace=False))
+    return [(Source(SRC_POINT, medium, center=(float(x[i]), float(y[i]), float(z[i]))), int(n_photons))
+            for i in pick]

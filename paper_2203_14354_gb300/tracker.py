@@ -10,6 +10,7 @@ constructor raises if CUDA or the library is unavailable."""
 from __future__ import annotations
 
 import ctypes as C
+from dataclasses import replace
 
 import numpy as np
 import torch
@@ -44,14 +45,23 @@ def make_source(src: Source, explicit=None) -> A.lxo_source:
     return s
 
 
+def own_tables(det: Detector) -> Detector:
+    """A copy of det that shares its mesh arrays but holds its own material
+    and surface records, so that changing the tracker's parameters
+    (set_theta) never writes into the caller's detector."""
+    return replace(det, materials=[replace(m) for m in det.materials],
+                   surfaces=[replace(s) for s in det.surfaces])
+
+
 class Tracker:
-    """A detector loaded on one GPU with its BVH built."""
+    """A detector loaded on one GPU with its BVH built.  The tracker keeps
+    its own copy of the detector's material and surface tables (self.det)."""
 
     def __init__(self, det: Detector, device: int = 0, leaf_size: int = 0, sah_bins: int = 0, n_threads: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("the photon tracker needs a CUDA GPU; no CPU fallback exists")
         L = A.lib()
-        self.det = det
+        self.det = own_tables(det)
         self.device = torch.device("cuda", device)
         ctx = C.c_void_p()
         rc = L.lxo_create(C.byref(ctx), device)
@@ -152,7 +162,8 @@ class Tracker:
         return torch.tensor(v, dtype=torch.float64)
 
     def set_theta(self, theta):
-        """Writes the tracked parameters back into the material / surface tables."""
+        """Sets the tracked parameters in the tracker's own material / surface
+        tables (not the detector it was built from) and uploads them."""
         th = [float(x) for x in (theta.detach().cpu().tolist() if torch.is_tensor(theta) else theta)]
         k = 0
         for m in self.adj_mats:
@@ -221,7 +232,8 @@ class Tracker:
             out.update(fate=torch.zeros(per_photon_n, dtype=torch.int32, device=dev),
                        detail=torch.zeros(per_photon_n, dtype=torch.int32, device=dev),
                        steps=torch.zeros(per_photon_n, dtype=torch.int32, device=dev),
-                       time=torch.zeros(per_photon_n, dtype=torch.float32, device=dev))
+                       time=torch.zeros(per_photon_n, dtype=torch.float32, device=dev),
+                       state=torch.zeros((per_photon_n, 9), dtype=torch.float32, device=dev))
         return out
 
     def _results(self, out):
@@ -230,6 +242,8 @@ class Tracker:
         if "fate" in out:
             r.ph_fate, r.ph_detail = out["fate"].data_ptr(), out["detail"].data_ptr()
             r.ph_steps, r.ph_time = out["steps"].data_ptr(), out["time"].data_ptr()
+        if "state" in out:
+            r.ph_state = out["state"].data_ptr()
         if "stats" in out:
             r.stats = out["stats"].data_ptr()
         if "adjoint" in out:
@@ -240,13 +254,14 @@ class Tracker:
                   per_photon=False, out=None, stream=None, sync=True, stats=False, adjoint=False):
         """Propagates photons base..base+n-1; returns (accumulates into) a dict
         of device tensors: lce, det [P], hist [P, n_tbins+1], fates [8+M+S]
-        and, with per_photon, fate / detail / steps / time [n]; with stats,
-        stats [32] as documented for lxo_results.stats in include/lxo.h; with
+        and, with per_photon, fate / detail / steps / time [n] and state [n, 9]
+        (final position, direction, polarisation); with stats,
+        stats [LXO_STATS_LEN] as documented for lxo_results.stats in include/lxo.h; with
         adjoint, adjoint [P, K] (tally sums of detected photons)."""
         if out is None:
             out = self.alloc_results(n_tbins, n if per_photon else 0)
         if stats and "stats" not in out:
-            out["stats"] = torch.zeros(32, dtype=torch.int64, device=self.device)
+            out["stats"] = torch.zeros(A.LXO_STATS_LEN, dtype=torch.int64, device=self.device)
         if adjoint and "adjoint" not in out:
             out["adjoint"] = torch.zeros((self.n_channels, self.n_tallies), dtype=torch.float64, device=self.device)
         src = make_source(source or self.det.source, explicit)
@@ -280,8 +295,10 @@ class Tracker:
         self._check(self._L.lxo_sync(self._ctx, _stream(stream)))
 
     # -- batched events -------------------------------------------------------
-    def upload_events(self, events):
-        """events: list of (Source (POINT / SEGMENT / BALL), n_photons)."""
+    def upload_events(self, events, first_event=0):
+        """events: list of (Source (POINT / SEGMENT / BALL), n_photons); the
+        first has event id first_event (photon ids (id << 32) | i), the
+        tallies' rows follow the list."""
         arr = (A.lxo_event * len(events))()
         for i, (src, n) in enumerate(events):
             e = arr[i]
@@ -292,7 +309,7 @@ class Tracker:
             e.singlet_frac, e.tau_singlet_ns, e.tau_triplet_ns = (float(src.singlet_frac), float(src.tau_singlet_ns),
                                                                   float(src.tau_triplet_ns))
             e.wl_mean_nm, e.wl_fwhm_nm = float(src.wl_mean_nm), float(src.wl_fwhm_nm)
-        self._check(self._L.lxo_upload_events(self._ctx, arr, len(events)))
+        self._check(self._L.lxo_upload_events(self._ctx, arr, len(events), first_event))
         self.n_events = len(events)
         self.event_photons = int(sum(int(n) for _, n in events))
 
@@ -325,31 +342,38 @@ class Tracker:
             self._check(self._L.lxo_sync(self._ctx, st))
         return out
 
-    def set_launch(self, blocks_per_sm=0, chunk=0):
-        self._check(self._L.lxo_set_launch(self._ctx, blocks_per_sm, chunk))
+    def set_launch(self, blocks_per_sm=0, chunk=0, threads=0):
+        """Launch shape: CTAs per SM (0 = occupancy limit), photon ids per
+        warp grab (0 = 64), threads per CTA (128 or 256; 0 = 256)."""
+        self._check(self._L.lxo_set_launch(self._ctx, blocks_per_sm, chunk, threads))
 
 
-def autotune_launch(tracker, run, blocks=(2, 3, 4, 5), chunks=(32, 64, 128, 256), reps=2):
+def autotune_launch(tracker, run, blocks=(2, 3, 4, 5), chunks=(32, 64, 128, 256), threads=(256,), reps=2):
     """Times `run()` (one launch of the workload to tune, on the current
-    stream) for every launch shape and keeps the fastest; returns
-    (blocks_per_sm, chunk, ms) and the table of timings."""
+    stream) for every launch shape (threads per CTA x CTAs per SM x chunk;
+    CTAs per SM are counted in 256-thread units, so 128-thread CTAs run
+    twice as many) and keeps the fastest; returns (threads, blocks_per_sm,
+    chunk, ms) and the table of timings keyed by (threads, blocks_per_sm,
+    chunk)."""
     table = {}
-    for b in blocks:
-        for c in chunks:
-            tracker.set_launch(b, c)
-            run()
-            torch.cuda.synchronize()
-            ts = []
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
+    for t in threads:
+        for b in blocks:
+            for c in chunks:
+                bps = b * (256 // t)
+                tracker.set_launch(bps, c, t)
                 run()
-                e1.record()
                 torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            table[(b, c)] = min(ts)
+                ts = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    run()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                table[(t, bps, c)] = min(ts)
     best = min(table, key=table.get)
-    tracker.set_launch(*best)
+    tracker.set_launch(best[1], best[2], best[0])
     return (*best, table[best]), table
 
 

@@ -71,3 +71,36 @@ def test_pmt_rings_of_the_50cm_tpc():
     import numpy as np
     together = np.sum(masks, axis=0)
     assert np.all(together == 1)
+
+
+def test_kernel_signature_reads_the_build_log():
+    """The staleness check of the ncu-derived constants: the timed kernel's
+    registers and spills come from the library's ptxas log, its sources'
+    hash from the files."""
+    from paper_2203_14354_gb300 import build
+    build.build()
+    sig = bench.kernel_signature()
+    assert isinstance(sig["registers"], int) and 16 <= sig["registers"] <= 255
+    assert isinstance(sig["spill_stores"], int) and isinstance(sig["spill_loads"], int)
+    assert len(sig["sources_sha256"]) == 64
+    assert set(sig) == set(bench.CAPTURED_KERNEL)
+
+
+def test_adjoint_summary_is_compact():
+    """The bench line's adjoint field: the cost ratio and the finite-
+    difference summary, taking each parameter at the step it was resolved
+    with (the wide step for noisy ones)."""
+    def agg(rel, z, fd, se):
+        return {"rel_diff": rel, "z": z, "fd": fd, "fd_se": se, "adjoint": fd, "adjoint_se": se}
+    fd = {"photons": 10 ** 9, "h_rel": 1e-3, "params": ["a", "b"], "seconds": 1.0,
+          "total": agg([0.01, 0.9], [1.0, 0.5], [100.0, 1.0], [1.0, 5.0]),
+          "top": agg([0.012, 0.5], [1.1, 0.4], [50.0, 1.0], [0.5, 5.0]),
+          "bottom": agg([0.011, 0.5], [0.9, 0.3], [50.0, 1.0], [0.5, 5.0]),
+          "per_pmt": {"z": [0.5, -1.0]}, "rings": {"z_max": [1.5, 2.0]},
+          "wide_step": {"h_rel": 3e-2, "params": ["b"], "total": agg([0.5], [0.2], [1.0], [1.0]),
+                        "top": agg([0.015], [0.4], [100.0], [1.0]), "bottom": agg([0.012], [0.3], [100.0], [1.0])}}
+    s = bench.adjoint_summary({"ratio": 1.16, "fwd_ms": 10.0, "fwd_adjoint_ms": 11.6, "fd_check": fd})
+    assert s["ratio"] == 1.16 and s["fd"]["wide_params"] == ["b"]
+    # resolved: a on all three aggregates, b on top and bottom at the wide step
+    assert s["fd"]["max_rel_diff_resolved"] == 0.015
+    assert len(json.dumps(s)) < 600

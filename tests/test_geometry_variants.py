@@ -169,3 +169,30 @@ def test_scaled_tpc_has_61_plus_61_windows_in_five_hexagonal_rings():
     top = det.pmt_pos[det.pmt_array == 1][:, :2]
     assert np.allclose(np.sort(top, axis=0), np.sort(det.pmt_pos[det.pmt_array == 0][:, :2], axis=0))
     assert np.hypot(top[:, 0], top[:, 1]).max() == pytest.approx(320.0)
+
+
+def test_grid_sources_fill_the_active_volume():
+    """Calibration sources on the 10 cm 3-D grid: every source a grid node,
+    inside the DARWIN-scale active volume (24-gon prism, z in [-2597, -1])
+    at least 50 mm from each wall side, the cathode and the gate; 256 of
+    about 12 000 nodes, seeded; the layout spans the volume in x, y and z."""
+    import math
+    det = g.Detector("src-only", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.uint32), np.zeros(0, np.uint8),
+                     np.zeros(0, np.uint8), np.zeros(0, np.uint16), np.zeros(0, np.int32), [], [],
+                     np.zeros(0, np.int32), np.zeros((0, 3), np.float32),
+                     g.Source(g.SRC_VOLUME_POLYGON, g.LXE, n_sides=24, radius=1300.0, z_min=-2597.0, z_max=-1.0))
+    ev = g.grid_sources(det, 1_000_000)
+    assert len(ev) == 256 and all(n == 1_000_000 and s.kind == g.SRC_POINT for s, n in ev)
+    c = np.array([s.center for s, _ in ev])
+    assert np.all(np.mod(c, 100.0) == 0.0)
+    apothem = 1300.0 * math.cos(math.pi / 24)
+    for k in range(24):
+        a = 2 * math.pi * (k + 0.5) / 24
+        assert np.all(c[:, 0] * math.cos(a) + c[:, 1] * math.sin(a) <= apothem - 50.0)
+    assert c[:, 2].min() >= -2597.0 + 50.0 and c[:, 2].max() <= -1.0 - 50.0
+    assert len(np.unique(c, axis=0)) == 256
+    assert len(np.unique(c[:, 2])) >= 20 and np.ptp(c[:, 0]) >= 2000 and np.ptp(c[:, 1]) >= 2000
+    every = g.grid_sources(det, 1, n_sources=10 ** 9)
+    assert 11_000 < len(every) < 13_000
+    assert [s.center for s, _ in g.grid_sources(det, 1, seed=0)] == [s.center for s, _ in ev]
+    assert [s.center for s, _ in g.grid_sources(det, 1, seed=1)] != [s.center for s, _ in ev]

@@ -11,6 +11,7 @@ import oracle as O
 from paper_2203_14354_gb300 import geometry as g
 from paper_2203_14354_gb300 import _capi as A
 from paper_2203_14354_gb300._capi import LxoError
+from tests.paired import sign_test
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +31,11 @@ def test_large_photon_ids_follow_the_oracle(small, base):
     ref = orc.propagate(n, base=base, seed=17, per_photon=True)
     fate_g = gpu["fate"].cpu().numpy()
     det_g = gpu["detail"].cpu().numpy()
-    same = (fate_g == ref["fate"]) & (det_g == ref["detail"])
-    assert same.mean() > 0.95, same.mean()
+    pt = sign_test(fate_g, det_g, ref["fate"], ref["detail"])
+    print("PARITY large_ids", base, pt)
+    assert pt["same"] > 0.99, pt   # measured 0.9942 - 0.9949
     lg, lo = gpu["lce"].cpu().numpy().sum(), ref["lce"].sum()
-    assert abs(int(lg) - int(lo)) <= 4 * np.sqrt(2.0 * lo) + 0.01 * lo
+    assert abs(int(lg) - int(lo)) <= 4 * np.sqrt(2.0 * lo)
 
 
 def test_invalid_arguments_are_rejected(small):

@@ -8,6 +8,7 @@ import torch
 
 import oracle as O
 from paper_2203_14354_gb300 import geometry as g
+from tests.paired import sign_test
 
 pytestmark = pytest.mark.gpu
 
@@ -48,21 +49,69 @@ def test_events_equal_single_source_runs(small_events):
     assert torch.equal(fates_sum, out["fates"])
 
 
+def test_event_ranges_reproduce_the_single_launch(small_events):
+    """Event-range sharding as one GPU runs it rank after rank (no
+    collective): each range uploaded with its first event's id gives the
+    single launch's rows bit for bit, and the fates sum to the single
+    launch's; the FP64 adjoint sums agree to rounding (their atomic adds
+    run in another order)."""
+    from paper_2203_14354_gb300.shard import event_ranges
+    det, trk, ev = small_events
+    trk.set_adjoint([g.LXE], [0, 1])
+    trk.upload_events(ev)
+    want = trk.propagate_events(seed=13, n_tbins=32, adjoint=True)
+    for world in (2, 3):
+        got = {k: torch.zeros_like(v) for k, v in want.items()}
+        for lo, hi in event_ranges([n for _, n in ev], world):
+            if hi == lo:
+                continue
+            trk.upload_events(ev[lo:hi], first_event=lo)
+            part = trk.propagate_events(seed=13, n_tbins=32, adjoint=True)
+            for k, v in part.items():
+                if k == "fates":
+                    got[k] += v
+                else:
+                    got[k][lo:hi] = v
+        for k in want:
+            if k == "adjoint":
+                assert torch.allclose(got[k], want[k], rtol=1e-12, atol=1e-9), world
+            else:
+                assert torch.equal(got[k], want[k]), (world, k)
+    trk.set_adjoint([], [])
+    trk.upload_events(ev)
+
+
 def test_events_parity_with_oracle(small_events):
+    """Per event, the light collected agrees with the oracle within 4 sigma
+    of the two-sample Poisson difference, and the total within 2 %.  Paired:
+    an event's photons are those of a single-source run with base e << 32
+    (bit for bit, test above), so the oracle's per-photon outcomes are
+    compared with the GPU's photon by photon; per (event, outcome) the
+    discordant photons split evenly (sign test)."""
     det, trk, ev = small_events
     out = trk.propagate_events(seed=9, n_tbins=64)
     orc = O.Oracle(det)
     lce_o = np.zeros((len(ev), det.n_pmts))
+    fg, dg, fo, do = [], [], [], []
     for e, (src, n) in enumerate(ev):
         if n:
-            lce_o[e] = orc.propagate(n, base=e << 32, seed=9, src=src)["lce"]
+            ref = orc.propagate(n, base=e << 32, seed=9, src=src, per_photon=True)
+            lce_o[e] = ref["lce"]
+            one = trk.propagate(n, base=e << 32, seed=9, source=src, per_photon=True, n_tbins=1)
+            fg.append(one["fate"].cpu().numpy())
+            dg.append(one["detail"].cpu().numpy().astype(np.int64) + (e << 20))
+            fo.append(ref["fate"])
+            do.append(ref["detail"].astype(np.int64) + (e << 20))
     lce_g = out["lce"].cpu().numpy()
     tot = lce_o.sum()
     assert abs(lce_g.sum() - tot) < 0.02 * tot
     for e, (_, n) in enumerate(ev):
         if n > 2000:
             a, b = lce_g[e].sum(), lce_o[e].sum()
-            assert abs(a - b) <= 4 * np.sqrt(2 * max(b, 1)) + 0.01 * b, e
+            assert abs(a - b) <= 4 * np.sqrt(2 * max(b, 1)), e
+    pt = sign_test(np.concatenate(fg), np.concatenate(dg), np.concatenate(fo), np.concatenate(do))
+    print("PARITY events_small", pt)
+    assert pt["same"] > 0.99, pt   # measured 0.9948
 
 
 def test_events_cuda_graph_and_launch_shape(small_events):
@@ -86,11 +135,23 @@ def test_events_cuda_graph_and_launch_shape(small_events):
         for k in ("lce", "det", "fates"):
             assert torch.equal(out[k], ref[k]), k
     trk.sync()
-    for b, c in ((1, 16), (3, 256), (0, 0)):
-        trk.set_launch(b, c)
+    for b, c, t in ((1, 16, 256), (3, 256, 256), (2, 32, 128), (10, 64, 128), (0, 0, 0)):
+        trk.set_launch(b, c, t)
         o = trk.propagate_events(seed=5, hist=False)
         for k in ("lce", "det", "fates"):
-            assert torch.equal(o[k], ref[k]), (b, c, k)
+            assert torch.equal(o[k], ref[k]), (b, c, t, k)
+    # the single-source kernel and the adjoint build too, in 128-thread CTAs
+    one = trk.propagate(20000, seed=6, per_photon=True)
+    trk.set_adjoint([g.LXE], [0])
+    adj = trk.propagate(20000, seed=6, adjoint=True)
+    trk.set_launch(0, 0, 128)
+    for k, v in trk.propagate(20000, seed=6, per_photon=True).items():
+        assert torch.equal(v, one[k]), k
+    adj128 = trk.propagate(20000, seed=6, adjoint=True)
+    assert torch.equal(adj128["det"], adj["det"])
+    assert torch.allclose(adj128["adjoint"], adj["adjoint"], rtol=1e-12, atol=1e-9)
+    trk.set_adjoint([], [])
+    trk.set_launch(0, 0, 0)
 
 
 def test_darwin_events_subset(tmp_path):
@@ -143,4 +204,5 @@ def test_darwin_events_full_size_sampled():
         gp = trk.propagate(m, base=e << 32, seed=4, source=src, per_photon=True, n_tbins=1)
         ref = orc.propagate(m, base=e << 32, seed=4, src=src, per_photon=True, n_tbins=1)
         same = (gp["fate"].cpu().numpy() == ref["fate"]) & (gp["detail"].cpu().numpy() == ref["detail"])
-        assert same.mean() > 0.9, (e, same.mean())
+        print("PARITY darwin_event", e, same.mean())
+        assert same.mean() > 0.99, (e, same.mean())   # measured 0.994 - 0.996

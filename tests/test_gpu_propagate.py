@@ -15,6 +15,8 @@ import torch
 
 import oracle as O
 from paper_2203_14354_gb300 import geometry as g
+from tests import closed_forms as CF
+from tests.paired import sign_test
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +29,13 @@ def Tracker():
 
 def np_out(out):
     return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+# floors of the share of photons ending alike on both sides, just under the
+# measured shares (small TPC 0.9945, DARWIN-scale 0.9948 - 0.9953 on GB300; a
+# diagnostic bound, the paired sign test is the criterion)
+SAME_SMALL = 0.99
+SAME_DARWIN = 0.99
 
 
 def sig2(p, n1, n2):
@@ -93,9 +102,13 @@ def test_small_tpc_parity_with_oracle(small):
     for c in range(det.n_pmts):
         p = do[c] / n
         assert abs(dg[c] - do[c]) / n <= 4 * sig2(p, n, n) + 1e-9
-    # same Philox stream per photon: most photons end identically
+    # same Philox stream per photon: most photons end identically (0.9945
+    # measured), and those that do not are as often the GPU's as the oracle's
+    # for every outcome (paired sign test, tests/paired.py)
+    pt = sign_test(gpu["fate"], gpu["detail"], ref["fate"], ref["detail"])
+    print("PARITY small_tpc", pt)
+    assert pt["same"] > SAME_SMALL, pt
     same = (gpu["fate"] == ref["fate"]) & (gpu["detail"] == ref["detail"])
-    assert same.mean() > 0.95, same.mean()
     # photons that end alike mostly took the same path: their arrival times agree
     # (a few end alike by coincidence after a rounding-level divergence)
     both = same & (gpu["fate"] == 0)
@@ -183,6 +196,40 @@ def test_gpu_total_internal_reflection_e2_e3(Tracker):
         assert (res["lce"][1] > 0) == want
 
 
+def test_gpu_two_interfaces_carry_the_refracted_polarisation(Tracker):
+    """An oblique beam polarised half-way between s and p crosses LXe ->
+    GXe -> quartz at 34 deg: the quartz window's reflectance depends on the
+    s / p mix left by the first refraction, so the top fraction checks the
+    kernel's transmitted polarisation against the exact reflection series
+    with amplitudes from Maxwell's boundary conditions (Sec. 2.2, Sec. 3)."""
+    trk = Tracker(g.layered_box())
+    n = 400_000
+    psi = math.radians(45.0)
+    ex = to_dev(CF.oblique_beam(n, 34.0, psi, -50.0), trk.device)
+    res = np_out(trk.propagate(n, source=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=ex))
+    top = CF.top_fraction(1.69, 1.0, 1.6, 34.0, math.cos(psi) ** 2)
+    assert abs(res["lce"][1] / n - top) < 4 * math.sqrt(top * (1 - top) / n), (res["lce"][1] / n, top)
+    assert res["lce"].sum() == n
+
+
+@pytest.mark.parametrize("psi_deg", [45.0, 70.0])
+def test_gpu_mirror_then_brewster_surface(Tracker, psi_deg):
+    """A beam heads down at the liquid surface's Brewster angle onto a
+    specular mirror of reflectivity 0.5, then up to the surface, where only
+    its s component reflects back to the lossy mirror: the top fraction
+    checks the kernel's mirrored polarisation against the exact series
+    (Sec. 2.2 reflector surfaces)."""
+    th = math.degrees(math.atan(1.0 / 1.69))
+    trk = Tracker(CF.mirror_floor_box(0.5))
+    n = 400_000
+    psi = math.radians(psi_deg)
+    ex = to_dev(CF.oblique_beam(n, th, psi, -50.0, up=False), trk.device)
+    res = np_out(trk.propagate(n, source=g.Source(g.SRC_EXPLICIT, g.LXE), explicit=ex))
+    top = CF.top_fraction(1.69, 1.0, 1.6, th, math.cos(psi) ** 2, first="mirror", mirror_floor=0.5)
+    assert abs(res["lce"][1] / n - top) < 4 * math.sqrt(top * (1 - top) / n), (res["lce"][1] / n, top)
+    assert res["fates"][4] == 0 and res["fates"][6] == 0
+
+
 @pytest.mark.parametrize("tau", [1.0, 0.1])
 def test_gpu_escape_from_absorbing_sphere(Tracker, tau):
     R = 100.0
@@ -243,8 +290,9 @@ def test_darwin_full_size_parity(darwin_pair):
     assert gpu["fates"][:7].sum() == n_gpu
     n_o = 20000
     ref = orc.propagate(n_o, seed=0, per_photon=True)
-    same = (gpu["fate"][:n_o] == ref["fate"]) & (gpu["detail"][:n_o] == ref["detail"])
-    assert same.mean() > 0.9, same.mean()
+    pt = sign_test(gpu["fate"][:n_o], gpu["detail"][:n_o], ref["fate"], ref["detail"])
+    print("PARITY darwin_sample", pt)
+    assert pt["same"] > SAME_DARWIN, pt
     lce_g = gpu["lce"].sum() / n_gpu
     lce_o = ref["lce"].sum() / n_o
     assert abs(lce_g - lce_o) < 4 * math.sqrt(lce_o * (1 - lce_o) / n_o) + 1e-3
@@ -277,7 +325,8 @@ def test_darwin_full_launch_sampled_ids(darwin_pair):
         ref = orc.propagate(100, base=base + int(s0), seed=1, per_photon=True, n_tbins=1)
         agree.append((fate[s0:s0 + 100] == ref["fate"]) & (detail[s0:s0 + 100] == ref["detail"]))
     agree = np.concatenate(agree)
-    assert agree.mean() > 0.9, agree.mean()
+    print("PARITY darwin_full_launch", agree.mean())
+    assert agree.mean() > SAME_DARWIN, agree.mean()
     assert starts[-1] > 0.9 * n  # the sample reaches the end of the launch
 
 
@@ -289,8 +338,21 @@ def test_darwin_every_pmt_within_4_sigma(darwin_pair):
     distributions within 0.01 in CDF."""
     det, trk, orc = darwin_pair
     n = 2_000_000
-    gpu = np_out(trk.propagate(n, base=3 << 30, seed=5, n_tbins=500))
-    ref = orc.propagate(n, base=3 << 30, seed=5, n_tbins=500)
+    gpu = np_out(trk.propagate(n, base=3 << 30, seed=5, n_tbins=500, per_photon=True))
+    ref = orc.propagate(n, base=3 << 30, seed=5, n_tbins=500, per_photon=True)
+    # paired: per outcome (each PMT's detections and QE failures, each
+    # material's and surface's losses) the discordant photons split evenly
+    pt = sign_test(gpu["fate"], gpu["detail"], ref["fate"], ref["detail"])
+    print("PARITY darwin_2e6", pt)
+    assert pt["same"] > SAME_DARWIN, pt
+    top = det.pmt_array == 1
+    for arr in (top, ~top):   # per array: detections and QE failures on its PMTs
+        chans = np.flatnonzero(arr)
+        for f in (0, 1):
+            sel_g = (gpu["fate"] == f) & np.isin(gpu["detail"], chans)
+            sel_o = (ref["fate"] == f) & np.isin(ref["detail"], chans)
+            a, b = int((sel_g & ~sel_o).sum()), int((sel_o & ~sel_g).sum())
+            assert abs(a - b) <= 4 * math.sqrt(max(a + b, 1)), (f, a, b)
     for key in ("lce", "det"):
         g_, o_ = gpu[key].astype(np.float64), ref[key].astype(np.float64)
         p = o_ / n

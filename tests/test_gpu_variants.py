@@ -10,6 +10,7 @@ import pytest
 
 import oracle as O
 from paper_2203_14354_gb300 import geometry as g
+from tests.paired import sign_test
 
 pytestmark = pytest.mark.gpu
 
@@ -19,11 +20,11 @@ N = 200_000
 def run_both(det, seed=4):
     from paper_2203_14354_gb300 import Tracker
     trk = Tracker(det)
-    out = trk.propagate(N, seed=seed)
-    lce_g = out["lce"].cpu().numpy().astype(np.float64)
+    out = {k: v.cpu().numpy() for k, v in trk.propagate(N, seed=seed, per_photon=True).items()}
     trk.close()
-    ref = O.Oracle(det).propagate(N, seed=seed)
-    return lce_g, ref["lce"].astype(np.float64)
+    ref = O.Oracle(det).propagate(N, seed=seed, per_photon=True)
+    pair = (out["fate"], out["detail"], ref["fate"], ref["detail"])
+    return out["lce"].astype(np.float64), ref["lce"].astype(np.float64), pair
 
 
 @pytest.fixture(scope="module")
@@ -39,12 +40,19 @@ def results():
 
 @pytest.mark.parametrize("name", ["baseline", "single_phase", "no_bottom_array", "paper_electrodes"])
 def test_variant_parity_with_oracle(results, name):
-    det, a, b = results[name]
+    """Per array within 4 sigma of the two-sample Poisson difference; paired
+    per outcome (sign test of the discordant photons)."""
+    det, a, b, pair = results[name]
     top = det.pmt_array == 1
     for sel in (top, ~top):
         if sel.any():
             x, y = a[sel].sum(), b[sel].sum()
-            assert abs(x - y) <= 4 * np.sqrt(2 * max(y, 1.0)) + 0.01 * y, (name, x, y)
+            assert abs(x - y) <= 4 * np.sqrt(2 * max(y, 1.0)), (name, x, y)
+    pt = sign_test(*pair)
+    print("PARITY variant", name, pt)
+    # measured 0.9957 - 0.9977; 0.974 with the paper's parallel wires, whose
+    # many grazing wire edges let rounding decide more hits
+    assert pt["same"] > (0.96 if name == "paper_electrodes" else 0.99), pt
 
 
 def test_variant_directions(results):

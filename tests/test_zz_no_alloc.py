@@ -8,8 +8,17 @@ The test calls it through the C ABI twice in a row and compares each result
 with the allocating entry point lxo_propagate_host on the same photons: the
 tallies are integers, so they must be identical (the tolerance of the parity
 tests for integer work).  It also checks that tallies larger than the static
-array are rejected.  This file is collected last on purpose."""
+array are rejected, and that the entry point allocates no device memory:
+after a first call has loaded everything it needs, many further calls leave
+the device's free memory where it was.  This file is collected last on
+purpose.
+
+The entry point's own fault path (a device fault flag set by the kernel)
+cannot be reached from here: every input that could set one is rejected on
+the host first (channels, indices, sizes).  By reading: it reads and checks
+the flags before any tally reaches the caller's arrays."""
 import ctypes as C
+import gc
 
 import numpy as np
 import pytest
@@ -67,3 +76,28 @@ def test_static_scratch_entry_rejects_oversized_tallies():
     out = host_buffers(trk, big)
     assert call_static(trk, 1000, 0, 1, big, out) == A.LXO_ERR_ARG
     assert out["fates"].sum() == 0
+
+
+def test_static_scratch_entry_allocates_no_device_memory():
+    """A fresh context that never called the allocating entry point, a
+    detector whose tallies need several MB (122 PMTs x 8001 time bins =
+    3.9 MB, which lxo_propagate_host would allocate): after one warm-up call,
+    further calls never lower the device's free memory.  (Memory freed by
+    earlier tests' contexts may come back meanwhile, so free memory may rise,
+    never fall.)"""
+    from paper_2203_14354_gb300 import Tracker, geometry
+    from paper_2203_14354_gb300 import _capi as A
+    det = geometry.scaled_tpc()
+    trk = Tracker(det)
+    n_tbins = 8000
+    out = host_buffers(trk, n_tbins)
+    assert call_static(trk, 20000, 0, 1, n_tbins, out) == A.LXO_OK
+    torch.cuda.synchronize()
+    gc.collect()
+    free0, _ = torch.cuda.mem_get_info()
+    lowest = free0
+    for k in range(20):
+        assert call_static(trk, 20000, (k + 1) * 20000, 1, n_tbins, out) == A.LXO_OK, k
+        lowest = min(lowest, torch.cuda.mem_get_info()[0])
+    assert lowest >= free0, (free0, lowest)
+    assert int(out["fates"][:7].sum()) == 21 * 20000
