@@ -435,7 +435,7 @@ def events_throughput(det, reps=3):
     trk.upload_events(ev[::10])
     sub = trk.alloc_event_results(256, hist=False)
     best, table = autotune_launch(trk, lambda: trk.propagate_events(seed=1, out=sub, hist=False, sync=False),
-                                  blocks=(3, 4, 5), chunks=(32, 64, 128), threads=(128, 256), reps=2)
+                                  blocks=(5, 6, 8), chunks=(32, 64, 128), threads=(128, 256), reps=2)
     del sub
     trk.upload_events(ev)
     out = trk.alloc_event_results(256, hist=True)

@@ -18,10 +18,10 @@
  *    by the caller, and must stay valid until the work queued on `stream`
  *    completes.  Geometry, BVH and scratch memory are owned by the context.
  *  - Calls that take `stream` (a cudaStream_t; NULL = the legacy default
- *    stream) are asynchronous.  Faults detected inside a kernel (traversal
- *    stack overflow, channel out of range, and in the bounds-checked build an
- *    index outside its array) set a device error word that lxo_sync() reads
- *    back and reports as LXO_ERR_DEVICE.
+ *    stream) are asynchronous.  Faults detected inside a kernel (channel out
+ *    of range, and in the bounds-checked build a traversal stack overflow or
+ *    an index outside its array) set a device error word that lxo_sync()
+ *    reads back and reports as LXO_ERR_DEVICE.
  *  - Result tallies ACCUMULATE: the caller zeroes them.  Photon p's random
  *    stream depends only on (seed, p), so splitting a run into several calls
  *    with disjoint photon_id_base ranges adds up to the same tallies.
@@ -36,7 +36,9 @@
  * sampling uses step = 0xFFFFFFFF.  In step s, draw 0 gives
  * u0 -> absorption distance -L_abs ln u0, u1 -> Rayleigh distance
  * -L_ray ln u1, u2 -> first surface decision, u3 -> second surface decision;
- * draw 1 (and 2, 3, ... for Rayleigh rejection tries) gives new directions.
+ * draw 1 gives new directions (Rayleigh scattering: u0 -> the cosine c of the
+ * angle to the polarisation, c = 2 cos((acos(1 - 2 u0) + 4 pi) / 3), the
+ * inverse CDF of the dipole law; u1 -> the azimuth about the polarisation).
  * The emission-time draw of a source with a scintillation time profile is
  * (step 0xFFFFFFFF, draw 0xFFFFFFFF): u0 < singlet_frac picks the singlet
  * component, and the delay is -tau ln u1 of the component picked.  The same
@@ -281,7 +283,9 @@ lxo_status lxo_set_pmts(lxo_ctx* ctx, const lxo_pmt* p, uint32_t n);
 
 /* Builds the bounding-volume hierarchy on the host (binned SAH, all cores)
  * and uploads nodes and triangles to the device.  params may be NULL.
- * info (host, may be NULL) receives sizes and the build time. */
+ * info (host, may be NULL) receives sizes and the build time.  LXO_ERR_ARG if
+ * the forest is so deep that a traversal could overflow its fixed stack
+ * (depth + 33 >= 96 entries; the kernels then need no overflow test). */
 lxo_status lxo_build_bvh(lxo_ctx* ctx, const lxo_bvh_params* params, lxo_bvh_info* info);
 
 /* Closest hit for n rays (device arrays): smallest t in (0, tmax] over all
@@ -358,8 +362,8 @@ lxo_status lxo_propagate_events(lxo_ctx* ctx, const lxo_run_params* params, cons
 /* Launch shape of the propagation kernels (found by an autotuner):
  * threads per block, 128 or 256 (0 = 256; each has its own kernel build
  * with the same registers per thread, and 256 is used for LXO_FLAG_STATS);
- * blocks_per_sm in 1..the occupancy limit (0 = the limit; the limit is 5
- * blocks of 256 or 10 of 128); photon ids taken per warp from the work
+ * blocks_per_sm in 1..the occupancy limit (0 = the limit; the limit is 8
+ * blocks of 256 or 16 of 128); photon ids taken per warp from the work
  * queue, chunk in 1..4096 (0 = 64).  Results do not depend on the shape. */
 lxo_status lxo_set_launch(lxo_ctx* ctx, uint32_t blocks_per_sm, uint32_t chunk, uint32_t threads);
 

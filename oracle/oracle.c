@@ -565,31 +565,30 @@ void orc_mirror(const double k[3], const double eps[3], const double N[3], doubl
 }
 
 /* Rayleigh scattering of a linearly polarised photon (dipole law, Appendix
- * item 3): the new direction k' has density proportional to 1 - (k'.eps)^2;
- * the new polarisation is eps projected perpendicular to k'.  Sampled by
- * rejection from the isotropic distribution, one Philox call per try (draw
- * indices 1, 2, ...: u0 -> cos, u1 -> azimuth, u2 -> accept). */
+ * item 3): the new direction k' has density proportional to
+ * 1 - (k'.eps)^2 = sin^2(psi), psi the angle between k' and eps; the new
+ * polarisation is eps projected perpendicular to k'.  Sampled exactly in the
+ * frame whose pole is eps: c = cos(psi) has density (3/4)(1 - c^2) on
+ * [-1, 1], whose CDF (3 (c + 1) - (c^3 + 1)) / 4 = u0 is the cubic
+ * c^3 - 3c = 2 - 4 u0; its root in [-1, 1] is c = 2 cos((acos(1 - 2 u0) + 4 pi) / 3)
+ * (with c = 2 cos(x), c^3 - 3c = 2 cos(3x)).  The azimuth about eps is
+ * 2 pi u1, measured in the orthonormal basis onb(eps).  One Philox call:
+ * draw index 1 of the step. */
 void orc_rayleigh(const double k[3], const double eps[3], uint64_t pid, uint32_t step, uint64_t seed,
                   double k_out[3], double eps_out[3])
 {
     (void)k;
-    for (uint32_t tr = 0; tr < MAX_TRIES; ++tr) {
-        double u[4];
-        draw4(seed, pid, step, 1 + tr, u);
-        double c = 2.0 * u[0] - 1.0, sn = sqrt(fmax(0.0, 1.0 - c * c)), ph = TWO_PI * u[1];
-        double kk[3] = {sn * cos(ph), sn * sin(ph), c};
-        double ce = dot3(kk, eps);
-        if (!(u[2] < 1.0 - ce * ce)) continue;
-        double e[3] = {eps[0] - ce * kk[0], eps[1] - ce * kk[1], eps[2] - ce * kk[2]};
-        if (norm3(e) < 1e-6) continue;
-        normalize3(e);
-        memcpy(k_out, kk, sizeof kk);
-        memcpy(eps_out, e, sizeof e);
-        return;
-    }
-    /* unreachable in practice (probability 3^-64): keep the photon as it was */
-    memcpy(k_out, k, 3 * sizeof(double));
-    memcpy(eps_out, eps, 3 * sizeof(double));
+    double u[4];
+    draw4(seed, pid, step, 1, u);
+    double c = 2.0 * cos((acos(1.0 - 2.0 * u[0]) + 4.0 * PI_D) / 3.0);
+    double sn = sqrt(fmax(0.0, 1.0 - c * c)), ph = TWO_PI * u[1];
+    double e1[3], e2[3];
+    onb(eps, e1, e2);
+    for (int a = 0; a < 3; ++a) k_out[a] = c * eps[a] + sn * (cos(ph) * e1[a] + sin(ph) * e2[a]);
+    normalize3(k_out);
+    double ce = dot3(k_out, eps);
+    for (int a = 0; a < 3; ++a) eps_out[a] = eps[a] - ce * k_out[a];
+    normalize3(eps_out);
 }
 
 /* random linear polarisation perpendicular to unit k from angle alpha */

@@ -577,8 +577,12 @@ int build_bvh(const float* tri_v, uint32_t nt, const int32_t* cluster_of, int n_
     }
     if (main_leaf) {
         float4* f = &out->nodes[4ull * main_wrap];
+        // a one-leaf tree: the leaf in both slots, so the traversal never has
+        // to test for a missing child (the leaf is tested twice, the second
+        // test finding nothing closer)
         put_box(f, 0, nodes[main_tmp].b);
-        int32_t r4[4] = {child_ref(main_tmp), kEmptyChild, 0, 0};
+        put_box(f, 1, nodes[main_tmp].b);
+        int32_t r4[4] = {child_ref(main_tmp), child_ref(main_tmp), 0, 0};
         memcpy(&f[3], r4, 16);
     }
     out->main_root = main_tmp < 0 ? kEmptyChild : (main_leaf ? (int32_t)main_wrap : child_ref(main_tmp));

@@ -15,11 +15,11 @@ constexpr int kStackSize = 96;          // traversal stack entries (>= BVH depth
 constexpr int kMaxDepth = 90;           // builder depth limit
 constexpr uint32_t kSourceStep = 0xFFFFFFFFu;
 constexpr int kMaxTries = 64;
-constexpr int32_t kEmptyChild = INT32_MIN;  // child slot of a one-leaf root
+constexpr int32_t kEmptyChild = INT32_MIN;  // empty layer cell or main tree
 
-// device error word bits
-// device error bits: traversal stack overflow, PMT channel out of range,
-// an index out of its array (checked build only, LXO_CHECK_BOUNDS)
+// device error bits: traversal stack overflow and an index out of its array
+// (checked build only, LXO_CHECK_BOUNDS: the normal build's stack cannot
+// overflow, lxo_build_bvh bounds the depth), PMT channel out of range
 enum : int { kErrStack = 1, kErrChannel = 2, kErrBounds = 8 };
 
 // Node: 64 bytes, boxes of both children (x, y, z slabs) + child references.
@@ -27,8 +27,9 @@ enum : int { kErrStack = 1, kErrChannel = 2, kErrBounds = 8 };
 //   f[1] = (c0.lo.y, c0.hi.y, c1.lo.y, c1.hi.y)
 //   f[2] = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //   f[3] = (ref0, ref1, -, -) as int bits
-// ref >= 0: internal node index; ref < 0: leaf, ~ref = (first << 3) | (count - 1);
-// ref == kEmptyChild: no child.
+// ref >= 0: internal node index; ref < 0: leaf, ~ref = (first << 3) | (count - 1).
+// Every node has two children (a one-leaf tree repeats its leaf); kEmptyChild
+// marks an empty cell of a layer grid or an empty main tree.
 // Triangle record: 48 bytes = 3 float4: (v0.xyz, v1.x), (v1.yz, v2.xy),
 // (v2.z, id, attr, channel) -- id, attr and channel as int bits;
 // attr = mat_inner | mat_outer << 8 | surface << 16.

@@ -133,6 +133,17 @@ __device__ __forceinline__ WRay wray_setup(float3 o, float3 d)
     return r;
 }
 
+// The edge functions again in double, for when one of them rounded to zero
+// in float (Woop et al.'s fallback).  Out of line: it is rarely taken, and
+// inline it costs the hot leaf loop registers.
+__device__ __noinline__ void edges_fp64(float Ax, float Ay, float Bx, float By, float Cx, float Cy, float& U, float& V,
+                                        float& W)
+{
+    U = __double2float_rn(__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx)));
+    V = __double2float_rn(__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx)));
+    W = __double2float_rn(__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax)));
+}
+
 __device__ __forceinline__ bool wray_hit(const WRay& r, float4 a, float4 b, float4 c, float tmax, float& t_out)
 {
     // vertices v0 = a.xyz, v1 = (a.w, b.x, b.y), v2 = (b.z, b.w, c.x)
@@ -149,11 +160,7 @@ __device__ __forceinline__ bool wray_hit(const WRay& r, float4 a, float4 b, floa
     float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
     float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
     float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-    if (U == 0.0f || V == 0.0f || W == 0.0f) {
-        U = __double2float_rn(__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx)));
-        V = __double2float_rn(__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx)));
-        W = __double2float_rn(__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax)));
-    }
+    if (U == 0.0f || V == 0.0f || W == 0.0f) edges_fp64(Ax, Ay, Bx, By, Cx, Cy, U, V, W);
     if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
     const float det = __fadd_rn(__fadd_rn(U, V), W);
     if (det == 0.0f) return false;
@@ -336,14 +343,18 @@ __device__ void trav_run(const Scene& sc, TravState& ts, int* stack, int* err, C
             const float bn = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), 0.0f));
             const float bf = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), lim));
             const bool ha = an <= af;
-            const bool hb = (bn <= bf) && (cr.y != kEmptyChild);
+            const bool hb = bn <= bf;   // every node has two children (see the builder)
             if (!ha && !hb) {
                 node = stack[--sp];
             } else {
                 const bool a_first = ha && (!hb || an <= bn);
                 node = a_first ? cr.x : cr.y;
                 if (ha && hb) {
-                    if (sp >= kStackSize) {
+                    // lxo_build_bvh rejects a forest whose depth plus the <= 33
+                    // entries trav_begin pushes could reach kStackSize, so this
+                    // cannot fire; only the checked build keeps the test (in the
+                    // normal build the never-taken exit cost 5 % of the time)
+                    if (LXO_CHECK_BOUNDS && sp >= kStackSize) {
                         atomicOr(err, kErrStack);
                         node = kDone;
                         sp = 1;
@@ -618,24 +629,25 @@ __global__ void k_sample_source(const __grid_constant__ PropParams p, float* pos
 
 // Rayleigh scattering, dipole law: density of the new direction k' is
 // proportional to 1 - (k'.eps)^2; new polarisation = eps projected
-// perpendicular to k'.  Rejection from the isotropic distribution.
+// perpendicular to k'.  Sampled without a loop, in the frame whose pole is
+// eps: c = cos(k', eps) from the inverse of its CDF, the cubic c^3 - 3c =
+// 2 - 4 u0, c = 2 cos((acos(1 - 2 u0) + 4 pi) / 3); azimuth 2 pi u1 in
+// onb(eps).  With w the unit azimuthal vector, k' = c eps + s w and the
+// projection of eps perpendicular to k' is s (s eps - c w), s = sin.
 __device__ __forceinline__ void rayleigh(Photon& ph, uint64_t seed)
 {
-    for (int tr = 0; tr < kMaxTries; ++tr) {
-        const U4 u = draw4(seed, ph.pid, ph.step, 1 + tr);
-        const float c = 2.0f * u.u0 - 1.0f, sn = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-        float sp, cp;
-        sincospif(2.0f * u.u1, &sp, &cp);
-        const float3 k = f3(sn * cp, sn * sp, c);
-        const float ce = dot(k, ph.pol);
-        if (!(u.u2 < 1.0f - ce * ce)) continue;
-        const float3 e = ph.pol - ce * k;
-        const float l2 = dot(e, e);
-        if (l2 < 1e-12f) continue;
-        ph.dir = k;
-        ph.pol = rsqrtf(l2) * e;
-        return;
-    }
+    const U4 u = draw4(seed, ph.pid, ph.step, 1);
+    const float a = acosf(1.0f - 2.0f * u.u0) * 0.318309886183790672f;   // in units of pi
+    const float c = 2.0f * cospif((a + 4.0f) * (1.0f / 3.0f));
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    float sp, cp;
+    sincospif(2.0f * u.u1, &sp, &cp);
+    float3 e1, e2;
+    onb(ph.pol, e1, e2);
+    const float3 w = cp * e1 + sp * e2;
+    const float3 eps = ph.pol;
+    ph.dir = normalize(c * eps + s * w);
+    ph.pol = normalize(s * eps - c * w);
 }
 
 // Lambertian reflection about the incident-side normal N (draw 1 of the step)
@@ -682,10 +694,13 @@ __device__ __forceinline__ bool dielectric(Photon& ph, float3 N, float n1, float
     if (!tir) {
         ct = sqrtf(1.0f - st2);
         const float a = n1 * ci, b = n2 * ct, c2 = n2 * ci, d2 = n1 * ct;
-        rs = (a - b) / (a + b);
-        rp = (c2 - d2) / (c2 + d2);
-        ts = 2.0f * a / (a + b);
-        tp = 2.0f * a / (c2 + d2);
+        // one fast reciprocal per denominator (2 ulp; the physics is float32
+        // and statistical, unlike the exact intersection)
+        const float i1 = __fdividef(1.0f, a + b), i2 = __fdividef(1.0f, c2 + d2);
+        rs = (a - b) * i1;
+        rp = (c2 - d2) * i2;
+        ts = 2.0f * a * i1;
+        tp = 2.0f * a * i2;
         pr = cs * cs * rs * rs + cpv * cpv * rp * rp;
     }
     if (u < pr) {
@@ -734,6 +749,9 @@ __device__ __forceinline__ StepDraw begin_step(const PropParams& p, const Photon
     // elsewhere) in place of powf's exact-case handling
     if (kSpectral && mt.ray_exp != 0.0f)
         ray_len *= exp2f(mt.ray_exp * __log2f(ph.wl * (1.0f / LXO_REF_WAVELENGTH_NM)));
+    // the accurate logarithm: the fast one's absolute error near u = 1 biases
+    // the sampled distances by ~1e-4 mm, enough for the paired parity tests
+    // of the adjoint tallies to see it (measured, 2 % faster)
     sd.d_abs = isinf(mt.abs_len) ? INFINITY : -mt.abs_len * logf(u.u0);
     sd.d_ray = isinf(ray_len) ? INFINITY : -ray_len * logf(u.u1);
     sd.u2 = u.u2;
@@ -892,13 +910,14 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
 // persistent propagation kernel
 // ---------------------------------------------------------------------------
 // tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
-// idle; 5 CTAs of 256 threads per SM (48 registers) hide more L1/L2 latency
-// than 3 CTAs at 80 registers (+22 %) despite a few spills
+// idle; 8 CTAs of 256 threads per SM (32 registers, the SM's 2048 threads)
+// hide more latency than 6 (40 registers, +1.4 % time), 5 (48, +5.4 %) or
+// 4 (64, +9.8 %) despite their spills
 #ifndef LXO_REFILL_MIN
 #define LXO_REFILL_MIN 1
 #endif
 #ifndef LXO_MIN_BLOCKS
-#define LXO_MIN_BLOCKS 5
+#define LXO_MIN_BLOCKS 8
 #endif
 
 // Tally of one photon's fate: shared-memory fate counters, global per-channel

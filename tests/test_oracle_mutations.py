@@ -40,11 +40,14 @@ MUTANTS = [
      "double pr = tir ? 1.0 : cs * cs * f[0] * f[0] + cp * cp * f[1] * f[1];",
      "double pr = tir ? 1.0 : cs * cs * f[1] * f[1] + cp * cp * f[0] * f[0];",
      [PINS + "test_dielectric_geometry_and_polarisation", PINS + "test_brewster_reflection_is_s_polarised"]),
-    ("Rayleigh acceptance cos^2 instead of sin^2", "if (!(u[2] < 1.0 - ce * ce)) continue;",
-     "if (!(u[2] < ce * ce)) continue;", [PINS + "test_rayleigh_dipole_laws"]),
+    ("Rayleigh cosine from the wrong root of the cubic", "(acos(1.0 - 2.0 * u[0]) + 4.0 * PI_D) / 3.0",
+     "(acos(1.0 - 2.0 * u[0]) + 2.0 * PI_D) / 3.0", [PINS + "test_rayleigh_dipole_laws"]),
+    ("Rayleigh cosine uniform instead of the dipole law",
+     "double c = 2.0 * cos((acos(1.0 - 2.0 * u[0]) + 4.0 * PI_D) / 3.0);", "double c = 1.0 - 2.0 * u[0];",
+     [PINS + "test_rayleigh_dipole_laws"]),
     ("Rayleigh polarisation not projected off the new direction",
-     "double e[3] = {eps[0] - ce * kk[0], eps[1] - ce * kk[1], eps[2] - ce * kk[2]};",
-     "double e[3] = {eps[0], eps[1], eps[2]};", [PINS + "test_rayleigh_dipole_laws"]),
+     "for (int a = 0; a < 3; ++a) eps_out[a] = eps[a] - ce * k_out[a];",
+     "for (int a = 0; a < 3; ++a) eps_out[a] = eps[a];", [PINS + "test_rayleigh_dipole_laws"]),
     ("Lambert cos theta uniform instead of sqrt(u)", "double c = sqrt(u[0]), sn", "double c = u[0], sn",
      [PINS + "test_lambert_cosine_law"]),
     ("absorption distance drawn from the Rayleigh uniform",
