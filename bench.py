@@ -54,7 +54,7 @@ SCHEDULERS_PER_SM = 4
 # signature and the SHA-256 of its sources.  When the built kernel differs,
 # the line says roofline.stale = true and drops traffic (the counters must
 # be taken again).
-TIMED_KERNEL = "_ZN3lxo11k_propagateILb0ELb0ELb0ELi256EEEvNS_10PropParamsE"   # k_propagate<0,0,0,256>
+TIMED_KERNEL = "_ZN3lxo11k_propagateILb0ELb0ELb0ELi256ELi8EEEvNS_10PropParamsE"   # k_propagate<0,0,0,256,8>
 KERNEL_SOURCES = ("paper_2203_14354_gb300/csrc/lxo_kernels.cu", "paper_2203_14354_gb300/csrc/lxo_internal.h")
 CAPTURED_KERNEL = {"registers": 48, "spill_stores": 264, "spill_loads": 292, "sources_sha256": None}
 
@@ -190,7 +190,8 @@ def adjoint_cost(args, n=10_000_000, reps=3):
     """Forward + adjoint against the plain forward on the 50 cm TPC with 61 +
     61 PMTs and thin-disk electrodes, 1e7 photons, 7 parameters: the time of
     the propagation with per-photon tallies (and the Jacobian kernel) over the
-    time of the plain propagation, same photons."""
+    time of the plain propagation, same photons, each at its faster register
+    budget (5 or 8 CTAs of 256 threads per SM)."""
     import torch
     from paper_2203_14354_gb300 import geometry, Tracker
     det = geometry.scaled_tpc()
@@ -206,24 +207,29 @@ def adjoint_cost(args, n=10_000_000, reps=3):
         if adj:
             trk.jacobian(out["adjoint"])
 
+    times, shapes, table = {}, {}, {}
     for adj in (False, True):
-        run(adj)
-    trk.sync()
-    times = {}
-    for adj in (False, True):
-        ts = []
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
+        for bps in (5, 8):
+            trk.set_launch(bps, 0, 256)
             run(adj)
-            b.record()
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        times[adj] = statistics.median(ts)
+            trk.sync()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                run(adj)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            table[f"{'adjoint' if adj else 'forward'} {bps} CTAs/SM"] = statistics.median(ts)
+            if adj not in times or statistics.median(ts) < times[adj]:
+                times[adj], shapes[adj] = statistics.median(ts), bps
+    trk.set_launch(0, 0, 0)
     trk.sync()
     res = {"workload": "50 cm dual-phase TPC, 61+61 PMTs, thin-disk gate/anode/cathode, 1e7 photons, 7 parameters",
            "fwd_ms": times[False], "fwd_adjoint_ms": times[True], "ratio": times[True] / times[False],
-           "fwd_photons_per_s": n / (times[False] / 1e3)}
+           "fwd_photons_per_s": n / (times[False] / 1e3),
+           "ctas_per_sm": {"forward": shapes[False], "adjoint": shapes[True]}, "ms_by_shape": table}
     if not args.no_adjoint_fd:
         res["fd_check"] = adjoint_fd_check(trk)
     return res
@@ -256,8 +262,9 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
     photons in 10 batches; mean and batch-means standard error of both
     estimates per parameter and aggregate.  Parameters whose differences are
     noisier than `noisy` (relative standard error) at h are differenced again
-    at h_wide: the noise of a common-random-number difference falls as
-    h^-1/2, its truncation error grows as h^2."""
+    at h_wide and h_wide / 2 and extrapolated (Richardson): the noise of a
+    common-random-number difference falls as h^-1/2, its truncation error
+    grows as h^2 and the extrapolation removes that term."""
     top = torch_bool(trk.det.pmt_array == 1, trk.device)
     theta0 = trk.theta()
     aggs = ("total", "top", "bottom")
@@ -297,10 +304,17 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
     for q in range(trk.n_params):
         differences(q, h, fd, fd_pmt)
     fd_w = np.full_like(fd, np.nan)
+    fd_half = np.full_like(fd, np.nan)
     wide = [q for q in range(trk.n_params)
             if np.max(fd[:, :, q].std(1, ddof=1) / math.sqrt(batches) / np.abs(fd[:, :, q].mean(1))) > noisy]
     for q in wide:
+        # Richardson extrapolation of the central difference, D(h) = f' +
+        # c h^2 + O(h^4): (4 D(h/2) - D(h)) / 3 cancels the h^2 term, which
+        # at a few per cent of theta exceeds the noise of the common-random-
+        # number differences
         differences(q, h_wide, fd_w)
+        differences(q, h_wide / 2, fd_half)
+        fd_w[:, :, q] = (4.0 * fd_half[:, :, q] - fd_w[:, :, q]) / 3.0
     trk.set_theta(theta0)
     names = ["L_abs_LXe", "L_ray_LXe", "R_PTFE_LXe", "R_PTFE_GXe", "T_gate", "T_anode", "T_cathode"]
     out = {"photons": batches * n_batch, "h_rel": h, "params": names[:trk.n_params],
@@ -350,7 +364,8 @@ def adjoint_fd_check(trk, batches=10, n_batch=100_000_000, h=1e-3, seed=31, h_wi
     out["rings"] = {"labels": labels, "pitch_mm": pitch, **rings_out, "z_max": zr.max(0).tolist(),
                     "n_over_2": (zr > 2).sum(0).tolist()}
     if wide:
-        out["wide_step"] = {"h_rel": h_wide, "params": [names[q] for q in wide]}
+        out["wide_step"] = {"h_rel": h_wide, "richardson_h_rel": [h_wide, h_wide / 2],
+                            "params": [names[q] for q in wide]}
         for a, name in enumerate(aggs):
             c = compare(a, fd_w)
             out["wide_step"][name] = {k: [v[q] for q in wide] for k, v in c.items()}

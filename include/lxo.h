@@ -362,9 +362,12 @@ lxo_status lxo_propagate_events(lxo_ctx* ctx, const lxo_run_params* params, cons
 /* Launch shape of the propagation kernels (found by an autotuner):
  * threads per block, 128 or 256 (0 = 256; each has its own kernel build
  * with the same registers per thread, and 256 is used for LXO_FLAG_STATS);
- * blocks_per_sm in 1..the occupancy limit (0 = the limit; the limit is 8
- * blocks of 256 or 16 of 128); photon ids taken per warp from the work
- * queue, chunk in 1..4096 (0 = 64).  Results do not depend on the shape. */
+ * blocks_per_sm, counted in blocks of the chosen size: up to 5 (10 of 128)
+ * selects the build with 48 registers per thread, 6..8 (12..16) the one
+ * with 32; 0 = the occupancy limit of the 32-register build for the
+ * forward and of the 48-register build for LXO_FLAG_ADJOINT; photon ids
+ * taken per warp from the work queue, chunk in 1..4096 (0 = 64).  Results
+ * do not depend on the shape. */
 lxo_status lxo_set_launch(lxo_ctx* ctx, uint32_t blocks_per_sm, uint32_t chunk, uint32_t threads);
 
 /* Adjoint (an extension of the paper's method: it has no gradients; the

@@ -909,16 +909,18 @@ __device__ int photon_step(const PropParams& p, Photon& ph, int& detail, Counter
 // ---------------------------------------------------------------------------
 // persistent propagation kernel
 // ---------------------------------------------------------------------------
-// tuned on the DARWIN-scale workload (GB300): refill as soon as one lane is
-// idle; 8 CTAs of 256 threads per SM (32 registers, the SM's 2048 threads)
-// hide more latency than 6 (40 registers, +1.4 % time), 5 (48, +5.4 %) or
-// 4 (64, +9.8 %) despite their spills
+// Register budgets, as CTAs of 256 threads per SM: every flavour of the
+// kernel is built for both and the launch shape picks one.  On the
+// DARWIN-scale forward workload (GB300) 8 CTAs (32 registers, the SM's 2048
+// threads) hide more latency than 6 (40 registers, +1.4 % time), 5 (48,
+// +5.4 %) or 4 (64, +9.8 %) despite their spills; the adjoint build and the
+// small 50 cm TPC, whose BVH stays in L1, run faster with 48 registers.
+// Lanes refill as soon as one is idle.
 #ifndef LXO_REFILL_MIN
 #define LXO_REFILL_MIN 1
 #endif
-#ifndef LXO_MIN_BLOCKS
-#define LXO_MIN_BLOCKS 8
-#endif
+constexpr int kBudgetFull = 8;   // 32 registers
+constexpr int kBudgetWide = 5;   // 48 registers
 
 // Tally of one photon's fate: shared-memory fate counters, global per-channel
 // counts and arrival-time histogram, optional per-photon record and adjoint
@@ -975,10 +977,10 @@ __device__ __forceinline__ void tally(const PropParams& p, unsigned long long* s
 // from a warp-local chunk (ballot + prefix popcount), chunks of p.chunk ids
 // coming from the global work-queue head.  Source sampling and tallies thus
 // run on many lanes at once instead of one lane per iteration.
-// Built for CTAs of kThreads = 256 (LXO_MIN_BLOCKS per SM) or 128 threads
-// (twice as many CTAs): the same register budget per thread either way.
-template <bool kStats, bool kAdjoint, bool kSpectral, int kThreads>
-__global__ void __launch_bounds__(kThreads, kThreads >= 256 ? LXO_MIN_BLOCKS : 2 * LXO_MIN_BLOCKS)
+// Built for CTAs of kThreads = 256 (kBudget per SM) or 128 threads (twice as
+// many CTAs): the same registers per thread either way.
+template <bool kStats, bool kAdjoint, bool kSpectral, int kThreads, int kBudget>
+__global__ void __launch_bounds__(kThreads, kBudget * 256 / kThreads)
     k_propagate(const __grid_constant__ PropParams p)
 {
     Counters cnt{};
@@ -1090,16 +1092,20 @@ cudaError_t launch_sample_source(const PropParams& p, float* pos, float* dir, fl
     return cudaGetLastError();
 }
 
-template <int kThreads>
+template <int kThreads, int kBudget>
 static cudaError_t launch_propagate_t(const PropParams& p, int sms, cudaStream_t st)
 {
     const bool stats = (p.flags & LXO_FLAG_STATS) != 0;
     const bool adj = (p.flags & LXO_FLAG_ADJOINT) != 0;
-    auto kern = p.spectral ? (adj ? k_propagate<false, true, true, kThreads> : k_propagate<false, false, true, kThreads>)
-                           : (adj ? k_propagate<false, true, false, kThreads> : k_propagate<false, false, false, kThreads>);
-    if (stats)  // the counting build exists for the default block size only
-        kern = p.spectral ? (adj ? k_propagate<true, true, true, 256> : k_propagate<true, false, true, 256>)
-                          : (adj ? k_propagate<true, true, false, 256> : k_propagate<true, false, false, 256>);
+    auto kern = p.spectral ? (adj ? k_propagate<false, true, true, kThreads, kBudget>
+                                  : k_propagate<false, false, true, kThreads, kBudget>)
+                           : (adj ? k_propagate<false, true, false, kThreads, kBudget>
+                                  : k_propagate<false, false, false, kThreads, kBudget>);
+    if (stats)  // the counting build exists for the default shape only
+        kern = p.spectral ? (adj ? k_propagate<true, true, true, 256, kBudgetFull>
+                                 : k_propagate<true, false, true, 256, kBudgetFull>)
+                          : (adj ? k_propagate<true, true, false, 256, kBudgetFull>
+                                 : k_propagate<true, false, false, 256, kBudgetFull>);
     const int threads = stats ? 256 : kThreads;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -1112,13 +1118,26 @@ static cudaError_t launch_propagate_t(const PropParams& p, int sms, cudaStream_t
     return cudaGetLastError();
 }
 
+// The register budget: the wide one (48 registers) when the launch asks for
+// at most kBudgetWide CTAs of 256 threads per SM, or by default for the
+// adjoint build; else the full-occupancy one (32 registers).
+template <int kThreads>
+static cudaError_t launch_propagate_b(const PropParams& p, int sms, cudaStream_t st)
+{
+    const int per256 = 256 / kThreads;
+    const bool adj = (p.flags & LXO_FLAG_ADJOINT) != 0;
+    const bool wide = p.blocks_per_sm ? (int)p.blocks_per_sm <= kBudgetWide * per256 : adj;
+    return wide ? launch_propagate_t<kThreads, kBudgetWide>(p, sms, st)
+                : launch_propagate_t<kThreads, kBudgetFull>(p, sms, st);
+}
+
 cudaError_t launch_propagate(const PropParams& p, int device, cudaStream_t st)
 {
     if (p.n == 0) return cudaSuccess;
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    return p.block_threads == 128 ? launch_propagate_t<128>(p, sms, st) : launch_propagate_t<256>(p, sms, st);
+    return p.block_threads == 128 ? launch_propagate_b<128>(p, sms, st) : launch_propagate_b<256>(p, sms, st);
 }
 
 // ---------------------------------------------------------------------------

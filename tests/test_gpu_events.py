@@ -135,21 +135,25 @@ def test_events_cuda_graph_and_launch_shape(small_events):
         for k in ("lce", "det", "fates"):
             assert torch.equal(out[k], ref[k]), k
     trk.sync()
-    for b, c, t in ((1, 16, 256), (3, 256, 256), (2, 32, 128), (10, 64, 128), (0, 0, 0)):
+    # both register budgets (up to 5 CTAs of 256 per SM: 48 registers; more: 32)
+    for b, c, t in ((1, 16, 256), (3, 256, 256), (8, 64, 256), (2, 32, 128), (10, 64, 128), (16, 32, 128),
+                    (0, 0, 0)):
         trk.set_launch(b, c, t)
         o = trk.propagate_events(seed=5, hist=False)
         for k in ("lce", "det", "fates"):
             assert torch.equal(o[k], ref[k]), (b, c, t, k)
     # the single-source kernel and the adjoint build too, in 128-thread CTAs
+    # and in both register budgets
     one = trk.propagate(20000, seed=6, per_photon=True)
     trk.set_adjoint([g.LXE], [0])
     adj = trk.propagate(20000, seed=6, adjoint=True)
-    trk.set_launch(0, 0, 128)
-    for k, v in trk.propagate(20000, seed=6, per_photon=True).items():
-        assert torch.equal(v, one[k]), k
-    adj128 = trk.propagate(20000, seed=6, adjoint=True)
-    assert torch.equal(adj128["det"], adj["det"])
-    assert torch.allclose(adj128["adjoint"], adj["adjoint"], rtol=1e-12, atol=1e-9)
+    for b, t in ((0, 128), (16, 128), (8, 256), (5, 256)):
+        trk.set_launch(b, 0, t)
+        for k, v in trk.propagate(20000, seed=6, per_photon=True).items():
+            assert torch.equal(v, one[k]), (b, t, k)
+        other = trk.propagate(20000, seed=6, adjoint=True)
+        assert torch.equal(other["det"], adj["det"]), (b, t)
+        assert torch.allclose(other["adjoint"], adj["adjoint"], rtol=1e-12, atol=1e-9), (b, t)
     trk.set_adjoint([], [])
     trk.set_launch(0, 0, 0)
 
