@@ -92,6 +92,12 @@ MUTANTS = [
      "double as = tir ? cs : cs * f[0], ap = tir ? cp : cp * f[1];",
      "double as = tir ? cs : cs * f[0], ap = tir ? -cp : cp * f[1];",
      [PINS + "test_total_internal_reflection_keeps_the_polarisation_magnitudes"]),
+    ("random polarisation at a fixed angle", "double ca = cos(alpha), sa = sin(alpha);",
+     "double ca = 1.0, sa = 0.0 * alpha;",
+     [PINS + "test_random_polarisation_is_uniform_about_the_direction"]),
+    ("random polarisation angle over a quarter turn", "double ca = cos(alpha), sa = sin(alpha);",
+     "double ca = cos(0.25 * alpha), sa = sin(0.25 * alpha);",
+     [PINS + "test_random_polarisation_is_uniform_about_the_direction"]),
     ("volume source radius not square-rooted", "double r = R * sqrt(w[0]), a = TWO_PI * w[1];",
      "double r = R * w[0], a = TWO_PI * w[1];", [PINS + "test_volume_source_uniform_isotropic"]),
     ("source directions on a hemisphere", "draw4(seed, pid, SOURCE_STEP, 0, u);\n    double c = 2.0 * u[0] - 1.0",

@@ -813,6 +813,47 @@ def test_volume_source_uniform_isotropic():
     assert np.all(med == g.LXE)
 
 
+def _check_uniform_polarisation(k, eps, n_bins=5):
+    """A linear polarisation uniform in angle about the direction k has
+    E[(eps.a)^2 | k] = (1 - (k.a)^2) / 2 for every fixed unit axis a (the
+    mean of cos^2 over the angle); checked in bins of (k.a)^2 for the three
+    axes, within 5 standard errors."""
+    for a in range(3):
+        c2, e2 = k[:, a] ** 2, eps[:, a] ** 2
+        edges = np.quantile(c2, np.linspace(0, 1, n_bins + 1))
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            m = (c2 >= lo) & (c2 <= hi)
+            want = np.mean((1 - c2[m]) / 2)
+            got = e2[m].mean()
+            se = e2[m].std() / math.sqrt(m.sum())
+            assert abs(got - want) < 5 * se + 1e-4, (a, lo, hi, got, want, se)
+    # directions within 18 deg of a world axis: the polarisation's angle in
+    # the plane perpendicular to that axis, taken modulo pi (a polarisation
+    # is a line), is uniform
+    for a in range(3):
+        u, v = (a + 1) % 3, (a + 2) % 3
+        for sgn in (1.0, -1.0):
+            m = sgn * k[:, a] > 0.95
+            if m.sum() < 500:
+                continue
+            ang = np.mod(np.arctan2(eps[m, v], eps[m, u]), np.pi) / np.pi
+            assert stats.kstest(ang, "uniform").pvalue > 1e-4, (a, sgn)
+
+
+def test_random_polarisation_is_uniform_about_the_direction():
+    """Unpolarised light (Sec. 3: the sources emit random linear
+    polarisation; Lambertian reflection depolarises): the source's and the
+    Lambertian reflector's new polarisations are uniform in angle about
+    their directions."""
+    o = O.Oracle(g.small_tpc())
+    n = 200_000
+    pos, dirs, pol, med = o.sample_source(n, seed=3)
+    _check_uniform_polarisation(dirs, pol)
+    N = np.array([0.0, 0.0, 1.0])
+    out = [O.lambert(N, pid=i, step=2, seed=8) for i in range(40_000)]
+    _check_uniform_polarisation(np.array([x[0] for x in out]), np.array([x[1] for x in out]))
+
+
 def test_generated_meshes_are_closed():
     for det in (g.small_tpc(), g.scaled_tpc(), g.layered_box(), g.icosphere(10, 2), g.electrode_box()):
         t = det.tris.astype(np.int64)
