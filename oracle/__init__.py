@@ -9,7 +9,6 @@ detector description it consumes comes from the input module
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 
 import numpy as np

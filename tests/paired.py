@@ -45,21 +45,3 @@ def sign_test(fate_g, detail_g, fate_o, detail_o, z_max=4.0, min_pairs=1):
            if z.size else None}
     assert res["z_max"] < z_max, res
     return res
-
-
-def grouped_sign_test(fate_g, detail_g, fate_o, detail_o, group_of, z_max=4.0):
-    """The sign test on outcomes merged into groups (e.g. PMTs of one array):
-    group_of maps an outcome key to a group id or -1 (ignored)."""
-    g = outcome(fate_g, detail_g)
-    o = outcome(fate_o, detail_o)
-    diff = g != o
-    gg, go = group_of(g[diff]), group_of(o[diff])
-    groups = np.union1d(gg[gg >= 0], go[go >= 0])
-    zs = []
-    for k in groups:
-        a = int((gg == k).sum())
-        b = int((go == k).sum())
-        zs.append(abs(a - b) / np.sqrt(max(a + b, 1)))
-    zmax = max(zs) if zs else 0.0
-    assert zmax < z_max, (zmax, groups, zs)
-    return zmax
