@@ -425,11 +425,19 @@ def calibration_check():
     cal = calibrate.Calibration(trk, ev, target, model_scale=2)
     res = cal.fit(theta0)
     rec = torch.tensor(res["theta"], dtype=torch.float64)
-    sigma = cal.covariance(rec, seed=98).diagonal().sqrt()
-    pull = (rec - torch.tensor(truth, dtype=torch.float64)) / sigma
+    cov = cal.covariance(rec, seed=98)
+    sigma = cov.diagonal().sqrt()
+    dev = rec - torch.tensor(truth, dtype=torch.float64)
+    pull = dev / sigma
+    # the parameters are correlated (L_abs and R_PTFE both scale the total
+    # light): chi^2 of the deviation with the full covariance, 4 degrees of
+    # freedom, and the correlation matrix
+    chi2 = float(dev @ torch.linalg.solve(cov, dev))
+    corr = cov / (sigma[:, None] * sigma[None, :])
     return {"workload": "50 cm TPC, 64 point sources x 2e5 photons on a 5 cm 3-D grid (model 2x), 4 parameters",
             "params": ["L_abs_LXe_mm", "L_ray_LXe_mm", "R_PTFE_LXe", "R_PTFE_GXe"], "truth": truth,
             "start": theta0, "recovered": res["theta"], "sigma": sigma.tolist(), "pull": pull.tolist(),
+            "chi2": chi2, "dof": len(truth), "corr": corr.tolist(),
             "launches": res["launches"], "scoring_steps": res["scoring_steps"], "seconds": res["seconds"]}
 
 
@@ -741,7 +749,7 @@ def main():
             line["spectral"] = {"photons_per_s": spectral["photons_per_s"], "cost_ratio": r3(spectral["cost_ratio"])}
         if calibration is not None:
             line["calibration"] = {"pull": [r3(x) for x in calibration["pull"]],
-                                   "launches": calibration["launches"]}
+                                   "chi2_4dof": r3(calibration["chi2"]), "launches": calibration["launches"]}
         if adjoint is not None:
             line["adjoint"] = adjoint_summary(adjoint)
         print(json.dumps(line), flush=True)
