@@ -254,7 +254,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--model-scale", type=int, default=2)
     ap.add_argument("--truth", type=float, nargs=4, default=(30_000.0, 350.0, 0.97, 0.80))
-    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--seed", type=int, default=7, help="seed of the source layout and of the target hit maps")
+    ap.add_argument("--fit-seed", type=int, default=1000, help="first seed of the model launches of the fit")
     ap.add_argument("--layout", choices=("grid3d", "plane"), default="grid3d",
                     help="sources on a seeded subset of the 3-D grid nodes in the active LXe (default), or on a "
                          "grid in the plane y = 0")
@@ -278,9 +279,17 @@ def main(argv=None):
     target = hit_maps(trk, a.truth, seed=a.seed)
     cal = Calibration(trk, events, target, model_scale=a.model_scale)
     dev_truth, _ = cal.loss(torch.tensor(a.truth, dtype=torch.float64), seed=a.seed + 1)
-    res = cal.fit(theta0, steps=a.steps)
+    res = cal.fit(theta0, steps=a.steps, seed=a.fit_seed)
     dev_fit, _ = cal.loss(torch.tensor(res["theta"], dtype=torch.float64), seed=a.seed + 1)
-    sigma = cal.covariance(res["theta"], seed=a.seed + 2).diagonal().sqrt().tolist()
+    cov = cal.covariance(res["theta"], seed=a.seed + 2)
+    sigma = cov.diagonal().sqrt().tolist()
+    # chi^2 of the deviation from the truth with the full covariance (the
+    # parameters are correlated), and the deviation along the covariance's
+    # eigenvectors in their own standard deviations, tightest first
+    dev = torch.tensor(res["theta"], dtype=torch.float64) - torch.tensor(a.truth, dtype=torch.float64)
+    lam, vec = torch.linalg.eigh(cov)
+    chi2 = float(dev @ torch.linalg.solve(cov, dev))
+    z_eig = ((vec.T @ dev) / lam.sqrt()).tolist()
     photons_per_iter = sum(n for _, n in events) * a.model_scale
     print(json.dumps(dict(
         detector=a.detector, layout=a.layout, sources=len(events), photons_per_source=a.photons,
@@ -288,7 +297,8 @@ def main(argv=None):
         params=["L_abs_LXe_mm", "L_ray_LXe_mm", "R_PTFE_LXe", "R_PTFE_GXe"],
         truth=list(a.truth), start=theta0, recovered=res["theta"],
         rel_error=[(r - t) / t for r, t in zip(res["theta"], a.truth)], sigma=sigma,
-        pull=[(r - t) / sg for r, t, sg in zip(res["theta"], a.truth, sigma)],
+        pull=[(r - t) / sg for r, t, sg in zip(res["theta"], a.truth, sigma)], chi2=chi2, z_eigen=z_eig,
+        fit_seed=a.fit_seed,
         deviance_at_truth=dev_truth, deviance_at_fit=dev_fit, cells=int(target.numel()),
         steps=a.steps, scoring_steps=res["scoring_steps"], launches=res["launches"], seconds_fit=res["seconds"],
         seconds_per_launch=res["seconds"] / res["launches"],
