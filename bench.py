@@ -42,12 +42,12 @@ OPS_PER_NODE, OPS_PER_TRI, OPS_PHYSICS = 40, 50, 250
 N_SM, LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) per photon of the propagation kernel: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of one timed launch on 2e6
-# photons of this workload (8.904 GB + 5.413 GB), divided by 2e6; scales with
+# photons of this workload (8.398 GB + 4.592 GB), divided by 2e6; scales with
 # the photon count.  Most of the writes, and a third of the reads, are the
 # 32-register build's spills and traversal stack leaving L1 and L2.
-DRAM_BYTES_PER_PHOTON = 7159
+DRAM_BYTES_PER_PHOTON = 6495
 # warp instructions issued per photon step by the same capture
-# (smsp__inst_executed.sum 1.0786e10 over 5.147e7 steps); the issue-slot peak
+# (smsp__inst_executed.sum 1.0785e10 over 5.147e7 steps); the issue-slot peak
 # is 152 SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
 WARP_INST_PER_STEP = 209.6
 SCHEDULERS_PER_SM = 4
@@ -57,8 +57,8 @@ SCHEDULERS_PER_SM = 4
 # be taken again).
 TIMED_KERNEL = "_ZN3lxo11k_propagateILb0ELb0ELb0ELi256ELi8EEEvNS_10PropParamsE"   # k_propagate<0,0,0,256,8>
 KERNEL_SOURCES = ("paper_2203_14354_gb300/csrc/lxo_kernels.cu", "paper_2203_14354_gb300/csrc/lxo_internal.h")
-CAPTURED_KERNEL = {"registers": 32, "spill_stores": 540, "spill_loads": 652,
-                   "sources_sha256": "d696514fcd2622ca9d3243155c034753d2ae05eeb9fc46481172120fe37b1abd"}
+CAPTURED_KERNEL = {"registers": 32, "spill_stores": 538, "spill_loads": 616,
+                   "sources_sha256": "c3b6331dda54e45fc49425f6e90370e9bbfa57d2def044f9493fc0d2e1248259"}
 
 
 def parse():
