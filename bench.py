@@ -427,17 +427,14 @@ def calibration_check():
     rec = torch.tensor(res["theta"], dtype=torch.float64)
     cov = cal.covariance(rec, seed=98)
     sigma = cov.diagonal().sqrt()
-    dev = rec - torch.tensor(truth, dtype=torch.float64)
-    pull = dev / sigma
     # the parameters are correlated (L_abs and R_PTFE both scale the total
     # light): chi^2 of the deviation with the full covariance, 4 degrees of
-    # freedom, and the correlation matrix
-    chi2 = float(dev @ torch.linalg.solve(cov, dev))
-    corr = cov / (sigma[:, None] * sigma[None, :])
+    # freedom, beside the per-parameter pulls
+    st = calibrate.deviation_stats(rec, truth, cov)
     return {"workload": "50 cm TPC, 64 point sources x 2e5 photons on a 5 cm 3-D grid (model 2x), 4 parameters",
             "params": ["L_abs_LXe_mm", "L_ray_LXe_mm", "R_PTFE_LXe", "R_PTFE_GXe"], "truth": truth,
-            "start": theta0, "recovered": res["theta"], "sigma": sigma.tolist(), "pull": pull.tolist(),
-            "chi2": chi2, "dof": len(truth), "corr": corr.tolist(),
+            "start": theta0, "recovered": res["theta"], "sigma": sigma.tolist(), "pull": st["pull"],
+            "chi2": st["chi2"], "dof": len(truth), "z_eigen": st["z_eigen"], "corr": st["corr"],
             "launches": res["launches"], "scoring_steps": res["scoring_steps"], "seconds": res["seconds"]}
 
 

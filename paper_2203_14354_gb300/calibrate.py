@@ -62,6 +62,24 @@ def poisson_deviance(mu, k, floor=1e-3):
     return 2.0 * (mu - k + klog).sum()
 
 
+def deviation_stats(theta, truth, cov):
+    """How far an estimate lies from the truth under its covariance:
+    pulls (per parameter, in its own standard deviation), the chi^2 of the
+    whole deviation d^T C^-1 d (the parameters are correlated), the
+    deviation along the covariance's eigenvectors in their own standard
+    deviations (tightest first; their squares sum to chi^2) and the
+    correlation matrix."""
+    theta = torch.as_tensor(theta, dtype=torch.float64)
+    truth = torch.as_tensor(truth, dtype=torch.float64)
+    cov = torch.as_tensor(cov, dtype=torch.float64)
+    d = theta - truth
+    sigma = cov.diagonal().sqrt()
+    lam, vec = torch.linalg.eigh(cov)
+    return dict(pull=(d / sigma).tolist(), chi2=float(d @ torch.linalg.solve(cov, d)),
+                z_eigen=((vec.T @ d) / lam.sqrt()).tolist(),
+                corr=(cov / (sigma[:, None] * sigma[None, :])).tolist())
+
+
 def hit_maps(tracker, theta, seed):
     """Detected hits [E, P] of the tracker's uploaded events at theta (no
     gradient)."""
@@ -283,13 +301,7 @@ def main(argv=None):
     dev_fit, _ = cal.loss(torch.tensor(res["theta"], dtype=torch.float64), seed=a.seed + 1)
     cov = cal.covariance(res["theta"], seed=a.seed + 2)
     sigma = cov.diagonal().sqrt().tolist()
-    # chi^2 of the deviation from the truth with the full covariance (the
-    # parameters are correlated), and the deviation along the covariance's
-    # eigenvectors in their own standard deviations, tightest first
-    dev = torch.tensor(res["theta"], dtype=torch.float64) - torch.tensor(a.truth, dtype=torch.float64)
-    lam, vec = torch.linalg.eigh(cov)
-    chi2 = float(dev @ torch.linalg.solve(cov, dev))
-    z_eig = ((vec.T @ dev) / lam.sqrt()).tolist()
+    st = deviation_stats(res["theta"], a.truth, cov)
     photons_per_iter = sum(n for _, n in events) * a.model_scale
     print(json.dumps(dict(
         detector=a.detector, layout=a.layout, sources=len(events), photons_per_source=a.photons,
@@ -297,7 +309,7 @@ def main(argv=None):
         params=["L_abs_LXe_mm", "L_ray_LXe_mm", "R_PTFE_LXe", "R_PTFE_GXe"],
         truth=list(a.truth), start=theta0, recovered=res["theta"],
         rel_error=[(r - t) / t for r, t in zip(res["theta"], a.truth)], sigma=sigma,
-        pull=[(r - t) / sg for r, t, sg in zip(res["theta"], a.truth, sigma)], chi2=chi2, z_eigen=z_eig,
+        pull=st["pull"], chi2=st["chi2"], z_eigen=st["z_eigen"],
         fit_seed=a.fit_seed,
         deviance_at_truth=dev_truth, deviance_at_fit=dev_fit, cells=int(target.numel()),
         steps=a.steps, scoring_steps=res["scoring_steps"], launches=res["launches"], seconds_fit=res["seconds"],

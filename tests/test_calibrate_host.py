@@ -3,8 +3,10 @@ expected hits are a known smooth function of the four parameters: the
 unconstrained transforms invert each other, the deviance is zero at the
 target and its gradient is the Poisson score, and Adam through the autograd
 Function recovers the hidden parameters from noise-free and from noisy hit
-maps, and the cross-fitted Fisher information stays unbiased when the
-per-cell Jacobians are noisy."""
+maps, the cross-fitted Fisher information stays unbiased when the
+per-cell Jacobians are noisy, and the deviation statistics of an estimate
+(pulls, chi^2 with the full covariance, eigen-deviations) match a worked
+example."""
 import math
 
 import pytest
@@ -195,3 +197,21 @@ def test_cross_fitted_fisher_is_unbiased_under_noisy_jacobians():
     naive = torch.einsum("epq,epr->qr", Jn, Jn / mu[..., None])
     assert torch.all(naive.diagonal() > 3 * d)  # the square of one estimate: noise dominates
     assert torch.all((F.diagonal() - d).abs() < 0.25 * d), (F.diagonal(), d)
+
+
+def test_deviation_stats_of_a_correlated_estimate():
+    """chi^2 = d^T C^-1 d worked by hand for C = [[4, 2], [2, 3]] and
+    d = (1, -1): C^-1 = [[3, -2], [-2, 4]] / 8, so chi^2 = (3 + 4 + 4) / 8;
+    pulls d_i / sqrt(C_ii); the eigen-deviations square-sum to chi^2; a
+    deviation along an eigenvector shows in that component alone."""
+    st = cal.deviation_stats([11.0, 19.0], [10.0, 20.0], [[4.0, 2.0], [2.0, 3.0]])
+    assert math.isclose(st["chi2"], 11.0 / 8.0, rel_tol=1e-12)
+    assert st["pull"] == pytest.approx([0.5, -1.0 / math.sqrt(3.0)], rel=1e-12)
+    assert sum(z * z for z in st["z_eigen"]) == pytest.approx(11.0 / 8.0, rel=1e-12)
+    assert st["corr"][0][1] == pytest.approx(2.0 / math.sqrt(12.0), rel=1e-12)
+    cov = torch.tensor([[4.0, 2.0], [2.0, 3.0]], dtype=torch.float64)
+    lam, vec = torch.linalg.eigh(cov)
+    d = 2.0 * lam[0].sqrt() * vec[:, 0]   # two standard deviations along the tightest direction
+    st = cal.deviation_stats(d, torch.zeros(2, dtype=torch.float64), cov)
+    assert st["z_eigen"] == pytest.approx([2.0, 0.0], abs=1e-12)
+    assert st["chi2"] == pytest.approx(4.0, rel=1e-12)
