@@ -1098,24 +1098,24 @@ struct BatchSlot {
     }
 };
 
-// Persistent photon loop.  A lane whose photon reached its fate stays idle
-// until at least LXO_REFILL_MIN lanes of its warp are idle (or all are); then
-// the idle lanes record their tallies together and take the next photon ids
-// from a warp-local chunk (ballot + prefix popcount), chunks of p.chunk ids
-// coming from the global work-queue head.  Source sampling and tallies thus
-// run on many lanes at once instead of one lane per iteration.  In the
-// forward builds photons are made a batch at a time: when its buffer in
-// shared memory is empty, the warp makes the next kBatchN photons of its
-// chunk, one per lane, and lanes that need a photon take the next ones from
-// the buffer (a lane would otherwise make its photon alone, as about one
-// lane dies per pass of the loop; 5 % less time on the DARWIN-scale mesh).
-// In the forward builds lanes do not wait for the slowest query of their
-// warp: each pass of the loop traces until some lane has finished its query,
-// and the unfinished queries resume in the next pass beside the fresh ones
-// (on the DARWIN-scale mesh this raised the lanes active in the node loop
-// from 31 % to 45 % and in the leaf loop from 11 % to 20 %, 9 % less time).
-// The adjoint builds keep whole steps: their extra state made the resumable
-// loop 4 % slower on the 50 cm TPC, whose tree stays in L1.
+// Persistent photon loop.  A lane whose photon reached its fate records its
+// tallies and takes the next photon id of its warp's chunk (ballot + prefix
+// popcount); chunks of p.chunk ids come from the global work-queue head.  A
+// lane refills as soon as it is idle (LXO_REFILL_MIN = 1: waiting for more
+// idle lanes measured slower).
+// Forward builds:
+// * Lanes do not wait for the slowest query of their warp: each pass of the
+//   loop traces until some lane has finished its query, and the unfinished
+//   queries resume in the next pass beside the fresh ones (dynamic ray
+//   fetch; on the DARWIN-scale mesh the lanes active in the node loop rose
+//   from 31 % to 45 % and in the leaf loop from 11 % to 20 %, 9 % less time).
+// * Photons are made a batch at a time: about one lane dies per pass, so
+//   when its shared-memory buffer is empty the warp makes the next kBatchN
+//   photons of its chunk, one per lane, and lanes that need a photon take
+//   the next ones from the buffer (7 % less time).
+// Adjoint builds keep whole steps and make photons lane by lane: with their
+// tallies the resumable loop was 4 % slower on the 50 cm TPC, whose tree
+// stays in L1.
 // Built for CTAs of kThreads = 256 (kBudget per SM) or 128 threads (twice as
 // many CTAs): the same registers per thread either way.
 template <bool kStats, bool kAdjoint, bool kSpectral, int kThreads, int kBudget>
