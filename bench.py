@@ -42,14 +42,14 @@ OPS_PER_NODE, OPS_PER_TRI, OPS_PHYSICS = 40, 50, 250
 N_SM, LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) per photon of the propagation kernel: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of one timed launch on 2e6
-# photons of this workload (8.398 GB + 4.592 GB), divided by 2e6; scales with
+# photons of this workload (8.423 GB + 4.602 GB), divided by 2e6; scales with
 # the photon count.  Most of the writes, and a third of the reads, are the
 # 32-register build's spills and traversal stack leaving L1 and L2.
-DRAM_BYTES_PER_PHOTON = 6495
+DRAM_BYTES_PER_PHOTON = 6512
 # warp instructions issued per photon step by the same capture
-# (smsp__inst_executed.sum 1.0785e10 over 5.147e7 steps); the issue-slot peak
+# (smsp__inst_executed.sum 1.0792e10 over 5.147e7 steps); the issue-slot peak
 # is 152 SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
-WARP_INST_PER_STEP = 209.6
+WARP_INST_PER_STEP = 209.7
 SCHEDULERS_PER_SM = 4
 # The kernel build those two numbers were captured from: its ptxas
 # signature and the SHA-256 of its sources.  When the built kernel differs,
@@ -58,7 +58,7 @@ SCHEDULERS_PER_SM = 4
 TIMED_KERNEL = "_ZN3lxo11k_propagateILb0ELb0ELb0ELi256ELi8EEEvNS_10PropParamsE"   # k_propagate<0,0,0,256,8>
 KERNEL_SOURCES = ("paper_2203_14354_gb300/csrc/lxo_kernels.cu", "paper_2203_14354_gb300/csrc/lxo_internal.h")
 CAPTURED_KERNEL = {"registers": 32, "spill_stores": 538, "spill_loads": 616,
-                   "sources_sha256": "9e1d6c968af48b8ddd18f5cefa66133993a1e5c4692d9df7b712ff549ba81afb"}
+                   "sources_sha256": "1fa675c8893873eba0ba098175fb9ad1a31d29e08863aa4f1dad41da785a8a8a"}
 
 
 def parse():

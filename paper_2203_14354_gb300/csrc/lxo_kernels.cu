@@ -1058,15 +1058,17 @@ __device__ __forceinline__ bool warp_chunk(const PropParams& p, uint32_t lane, u
 }
 
 // A photon in a warp's batch buffer: word j of slot k at o[j * kBatchN + k]
-// (consecutive lanes, consecutive banks).  Only position, direction,
-// polarisation and id are kept; medium, emission time and wavelength follow
-// from the id and the source when the photon is taken, exactly as
-// make_photon computes them (a smaller buffer leaves more of the SM's memory
-// to L1: 1.5 % faster than keeping all 13 words).
+// (consecutive lanes, consecutive banks).  Position, direction,
+// polarisation, id and, in the spectral build, the wavelength are kept;
+// medium and emission time follow from the id and the source when the
+// photon is taken, exactly as make_photon computes them (a smaller buffer
+// leaves more of the SM's memory to L1: 1.5 % faster than keeping all 13
+// words; the wavelength's Box-Muller draw is too dear to redo one lane at a
+// time).
 constexpr int kBatchN = 32;
 template <bool kSpectral>
 struct BatchSlot {
-    static constexpr int kWords = 11;
+    static constexpr int kWords = kSpectral ? 12 : 11;
     static __device__ __forceinline__ void store(float* o, const Photon& q)
     {
         o[0 * kBatchN] = q.pos.x; o[1 * kBatchN] = q.pos.y; o[2 * kBatchN] = q.pos.z;
@@ -1074,6 +1076,7 @@ struct BatchSlot {
         o[6 * kBatchN] = q.pol.x; o[7 * kBatchN] = q.pol.y; o[8 * kBatchN] = q.pol.z;
         o[9 * kBatchN] = __uint_as_float((uint32_t)q.pid);
         o[10 * kBatchN] = __uint_as_float((uint32_t)(q.pid >> 32));
+        if (kSpectral) o[11 * kBatchN] = q.wl;
     }
     static __device__ __forceinline__ Photon load(const float* o, const PropParams& p)
     {
@@ -1086,12 +1089,11 @@ struct BatchSlot {
             const EventDev& ev = p.events[(uint32_t)(q.pid >> 32) - p.first_event];
             q.medium = ev.medium;
             q.time = ev.t0 + emission_delay(p, q.pid, ev.prof);
-            q.wl = kSpectral && p.spectral ? emission_wavelength(p, q.pid, ev.spec) : 0.0f;
         } else {
             q.medium = p.src.medium;
             q.time = p.src.t0 + emission_delay(p, q.pid, p.src.prof);
-            q.wl = kSpectral && p.spectral ? emission_wavelength(p, q.pid, p.src.spec) : 0.0f;
         }
+        q.wl = kSpectral ? o[11 * kBatchN] : 0.0f;
         q.last = LXO_NO_HIT;
         q.step = 0;
         return q;
