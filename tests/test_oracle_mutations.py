@@ -162,6 +162,14 @@ MUTANTS = [
      "uint32_t key[2] = {(uint32_t)(seed >> 32), (uint32_t)seed};", [PINS + "test_draw_contract"]),
     ("no spawn offset after a surface", "double eps = ldexp(m, -18);", "double eps = 0.0 * m;",
      [PINS + "test_total_internal_reflection_on_shared_edges"]),
+    ("polygon source accepts the circumscribed circle", "double ap = R * cos(PI_D / n);", "double ap = R;",
+     [PINS + "test_polygon_source_fills_the_polygon_uniformly"]),
+    ("polygon source sides at the vertex angles", "double a = phase + TWO_PI * (k + 0.5) / n;",
+     "double a = phase + TWO_PI * k / n;", [PINS + "test_polygon_source_fills_the_polygon_uniformly"]),
+    ("slab test without ordering the two plane distances", "if (ta > tb) { double x = ta; ta = tb; tb = x; }", "",
+     [PINS + "test_bvh_equals_brute_force_on_soup", PINS + "test_watertight_closed_sphere"]),
+    ("uniform without the half-step offset", "return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);",
+     "return ((double)(x >> 9)) * (1.0 / 8388608.0);", [PINS + "test_uniform_mapping_range"]),
     ("no special case at normal incidence",
      "if (norm3(s) < 1e-6) {\n        s[0] = eps[0]; s[1] = eps[1]; s[2] = eps[2];\n    } else {\n        normalize3(s);\n    }",
      "normalize3(s);", [PINS + "test_normal_incidence_keeps_photon", PINS + "test_worked_example_e1_reflection_series"]),

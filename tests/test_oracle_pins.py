@@ -813,6 +813,36 @@ def test_volume_source_uniform_isotropic():
     assert np.all(med == g.LXE)
 
 
+@pytest.mark.parametrize("n_sides, phase", [(6, 0.0), (6, 0.3), (24, 0.1)])
+def test_polygon_source_fills_the_polygon_uniformly(n_sides, phase):
+    """Positions of the polygon-prism source (the active volume of Sec. 3's
+    uniform photon sources): every point lies inside the regular polygon
+    whose vertices are R (cos, sin)(phase + 2 pi k / n), checked edge by edge
+    with cross products; the density is uniform over its area, so the share
+    inside the inscribed circle is pi a^2 / A with a = R cos(pi / n) and
+    A = n R^2 sin(2 pi / n) / 2, and each of the n sectors between the centre
+    and a side holds 1/n of the points; z is uniform."""
+    det = g.small_tpc()
+    R, n = 100.0, 60_000
+    src = g.Source(g.SRC_VOLUME_POLYGON, g.LXE, n_sides=n_sides, radius=R, phase=phase, z_min=-90.0, z_max=-10.0)
+    pos = O.Oracle(det).sample_source(n, seed=3, src=src)[0]
+    ang = phase + 2 * np.pi * np.arange(n_sides + 1) / n_sides
+    v = R * np.stack([np.cos(ang), np.sin(ang)], 1)
+    for k in range(n_sides):
+        e = v[k + 1] - v[k]
+        side = e[0] * (pos[:, 1] - v[k][1]) - e[1] * (pos[:, 0] - v[k][0])
+        assert side.min() >= -1e-9 * R * R, (k, side.min())
+    a = R * math.cos(math.pi / n_sides)
+    area = n_sides * R * R * math.sin(2 * math.pi / n_sides) / 2
+    p_in = math.pi * a * a / area
+    r = np.hypot(pos[:, 0], pos[:, 1])
+    assert abs((r < a).mean() - p_in) < 4 * binom_sigma(p_in, n)
+    sector = np.floor(np.mod(np.arctan2(pos[:, 1], pos[:, 0]) - phase, 2 * np.pi) / (2 * np.pi / n_sides))
+    counts = np.bincount(sector.astype(int), minlength=n_sides)
+    assert stats.chisquare(counts).pvalue > 1e-4
+    assert stats.kstest((pos[:, 2] + 90.0) / 80.0, "uniform").pvalue > 1e-4
+
+
 def _check_uniform_polarisation(k, eps, n_bins=5):
     """A linear polarisation uniform in angle about the direction k has
     E[(eps.a)^2 | k] = (1 - (k.a)^2) / 2 for every fixed unit axis a (the
